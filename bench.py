@@ -1,0 +1,360 @@
+"""Benchmark of the fused stream-and-collide step on B300 (one JSON line on stdout).
+
+Workload (default): D3Q19 lid-driven cavity 256^3 in FP64, Re 1000, lid u = 0.02 along x on
+the whole plane z = 255, bounce-back walls on the other faces, nu = u N / Re,
+omega = 1 / (3 nu + 1/2), AA pattern, SoA layout, BGK-W2 collision.  A step is one time
+iteration over the whole lattice.  The 2.5 GB population array is far larger than the
+126 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--lattice 19|27] [--n 256] [--scheme aa] [--collision BGK_W2]
+                  [--precision f64|f32|f16] [--matrix]
+
+MLUPS counts every lattice node (walls included), the paper's convention.  Under torchrun
+(N > 1) each rank runs an independent replica of the workload (replicas only: the method
+needs no data exchange between independent lattices); the value is the sum of all ranks'
+updates over the slowest rank's time.  --impl reference times the FP64 CPU oracle on the
+host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2010_11751_b300 import inputs as I  # noqa: E402
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--lattice", type=int, default=19)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--scheme", default="aa")
+    ap.add_argument("--collision", default="BGK_W2")
+    ap.add_argument("--precision", default="f64")
+    ap.add_argument("--reynolds", type=float, default=1000.0)
+    ap.add_argument("--matrix", action="store_true", help="also time every scheme x collision x lattice")
+    ap.add_argument("--matrix-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(MEASURED) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(args):
+    n = args.n
+    nu = I.cavity_nu(0.02, n, args.reynolds)
+    omega = 1.0 / (3.0 * nu + 0.5)
+    return n, omega, I.cavity_flags(n, n, n), {I.LID: (0.02, 0.0, 0.0)}
+
+
+def workload_name(args):
+    return (f"D3Q{args.lattice} lid-driven cavity {args.n}^3 {args.precision.upper()}, Re {args.reynolds:g}, "
+            f"{args.scheme} scheme, SoA, {args.collision}")
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 7:
+                    continue
+                try:
+                    sm.append(float(p[0]))
+                    smax = float(p[1])
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def time_native(args, rank, local, pg):
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    n, omega, flags, walls = workload(args)
+    N = n ** 3
+    g = L.Lattice(args.lattice, n, n, n, args.scheme, args.collision, omega, flags,
+                  precision=L.PRECISIONS[args.precision], wall_velocities=walls, stream=stream.cuda_stream)
+    g.init_equilibrium()
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            for s in range(args.steps):
+                g.step(1)
+                evs[s + 1].record(stream)
+        torch.cuda.synchronize()
+    per = [evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if pg is not None:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    m, e = g.reduce()
+    bpc = g.bytes_per_cell_update
+    # step kinds alternate for AA (even: local, odd: neighbour pull/push); the first timed
+    # step has the parity of the warm-up count
+    first = args.warmup % 2
+    odd = [t for s, t in enumerate(per) if (first + s) % 2 == 1]
+    even = [t for s, t in enumerate(per) if (first + s) % 2 == 0]
+    launches_per_step = 2 if args.scheme == "swap" else 1
+    res = dict(N=N, total_ms=total_ms, per=per, odd=odd, even=even, bpc=bpc, mass=m, energy=e,
+               clocks=clk.summary(), launches=args.steps * launches_per_step)
+    g.close()
+    if not args.no_e2e:
+        res["e2e"] = e2e_native(args, L, torch)
+    return res
+
+
+def e2e_native(args, L, torch):
+    """Same metric through the public C ABI with host buffers: host (rho, u) -> init, K x
+    (step + FP64 conserved sums read back), host (rho, u) read back at the end."""
+    n, omega, flags, walls = workload(args)
+    N = n ** 3
+    rho = torch.ones(N, dtype=torch.float64).pin_memory()
+    u = torch.zeros(3 * N, dtype=torch.float64).pin_memory()
+    rho_out = torch.empty(N, dtype=torch.float64).pin_memory()
+    u_out = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    g = L.Lattice(args.lattice, n, n, n, args.scheme, args.collision, omega, flags,
+                  precision=L.PRECISIONS[args.precision], wall_velocities=walls)
+    g.init_equilibrium(rho, u)  # first call allocates; not timed
+    g.step(args.warmup)
+    g.reduce()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.init_equilibrium(rho, u)
+    for _ in range(args.steps):
+        g.step(1)
+        g.reduce()
+    g.macroscopic(rho_out, u_out)
+    t1 = time.perf_counter()
+    g.close()
+    mlups = N * args.steps / (t1 - t0) / 1e6
+    return {"value": round(mlups, 2), "unit": "MLUPS", "h2d_bytes_per_step": int(32 * N / args.steps),
+            "d2h_bytes_per_step": int(16 + 32 * N / args.steps),
+            "note": "host rho/u upload, K x (step + FP64 mass/energy read back), host rho/u download"}
+
+
+def oracle_baseline(args, seconds, max_steps=None, warmup=0):
+    """The FP64 CPU oracle, as it stands, on the host cores: same workload, full lattice."""
+    import ctypes
+
+    from oracle import oracle as O
+
+    n, omega, flags, walls = workload(args)
+    N = n ** 3
+    threads = os.cpu_count() or 1
+    lat = O.Lattice(args.lattice, n, n, n, flags, args.collision, O.params(omega), walls)
+    lat.init_equilibrium()
+    out = np.zeros_like(lat.f)
+    lib = O.lib()
+    fl = lat.flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    steps, t_total = 0, 0.0
+    cur, nxt = lat.f, out
+    for _ in range(warmup):
+        lib.orc_step(args.lattice, n, n, n, fl, O._dp(lat.wall_u), O.MODELS[args.collision], O._dp(lat.prm),
+                     None, None, threads, O._dp(cur), O._dp(nxt))
+        cur, nxt = nxt, cur
+    while t_total < seconds and (max_steps is None or steps < max_steps):
+        t0 = time.perf_counter()
+        rc = lib.orc_step(args.lattice, n, n, n, fl, O._dp(lat.wall_u), O.MODELS[args.collision], O._dp(lat.prm),
+                          None, None, threads, O._dp(cur), O._dp(nxt))
+        t_total += time.perf_counter() - t0
+        if rc != 0:
+            raise RuntimeError("oracle step failed")
+        cur, nxt = nxt, cur
+        steps += 1
+    return {"value": round(N * steps / t_total / 1e6, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} full {n}^3 time steps of the same workload ({N * steps} cell updates, "
+                      f"{t_total:.1f} s)"}, steps, t_total
+
+
+def matrix(args):
+    """Every scheme x collision x lattice of the 256^3 cavity (FP64), a few steps each."""
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    n, omega, flags, walls = workload(args)
+    hbm, _ = peaks()
+    rows = []
+    for Q in (19, 27):
+        for scheme in ("twopop", "swap", "aa", "esotwist"):
+            for coll in ("BGK_W2", "TRT", "RR", "K"):
+                stream = torch.cuda.Stream()
+                g = L.Lattice(Q, n, n, n, scheme, coll, omega, flags, wall_velocities=walls,
+                              stream=stream.cuda_stream)
+                g.init_equilibrium()
+                g.step(2)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                g.step(args.matrix_steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.matrix_steps
+                mlups = n ** 3 / (ms * 1e-3) / 1e6
+                gbs = g.bytes_per_cell_update * n ** 3 / (ms * 1e-3) / 1e9
+                rows.append({"lattice": f"D3Q{Q}", "scheme": scheme, "collision": coll, "mlups": round(mlups, 1),
+                             "ms_per_step": round(ms, 3), "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)})
+                g.close()
+                del stream
+    return rows
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        W = args.warmup
+        base, steps, t = oracle_baseline(args, 1e30, max_steps=args.steps, warmup=W)
+        line = {"impl": "reference", "metric": f"MLUPS ({workload_name(args)})", "value": base["value"],
+                "unit": "MLUPS", "n_gpus": 0, "steps": steps, "warmup": W, "ms_per_step": round(1e3 * t / steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": workload_name(args), "lattice": f"D3Q{args.lattice}",
+                                                "n": args.n, "collision": args.collision},
+                "cpu_baseline": {"value": base["value"], "unit": "MLUPS", "cores": base["cores"], "kind": "oracle",
+                                 "sample": base["sample"]},
+                "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    r = time_native(args, rank, local, pg)
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    N, K = r["N"], args.steps
+    value = world * N * K / (r["total_ms"] * 1e-3) / 1e6
+    dominant = r["odd"] if (args.scheme == "aa" and r["odd"]) else r["per"]
+    dom_ms = sum(dominant) / len(dominant)
+    achieved = r["bpc"] * N / (dom_ms * 1e-3) / 1e9
+    line = {
+        "metric": f"MLUPS ({workload_name(args)})",
+        "value": round(value, 2),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(r["total_ms"] / K, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "lattice": f"D3Q{args.lattice}", "n": args.n,
+                   "scheme": args.scheme, "layout": "soa", "collision": args.collision, "reynolds": args.reynolds,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "no flush: population state larger than L2 (inputs larger than L2)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else ""),
+                     "bytes_per_cell_update": r["bpc"], "peak_source": f"{src} hbm_gbs"},
+        "hbm_frac_step": round(r["bpc"] * N * K / (r["total_ms"] * 1e-3) / 1e9 / hbm, 4),
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "conserved": {"mass": r["mass"], "energy": r["energy"]},
+    }
+    if args.scheme == "aa" and r["odd"] and r["even"]:
+        line["per_launch_ms"] = {"even": round(sum(r["even"]) / len(r["even"]), 4),
+                                 "odd": round(sum(r["odd"]) / len(r["odd"]), 4)}
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
+    if not args.no_cpu_baseline:
+        base, _, _ = oracle_baseline(args, args.cpu_seconds, max_steps=20)
+        line["cpu_baseline"] = base
+    if args.matrix:
+        line["matrix"] = matrix(args)
+    print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

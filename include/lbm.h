@@ -1,0 +1,183 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) lattice Boltzmann stream-and-collide
+ * library liblbm.so.
+ *
+ * Method: Latt, Coreixas & Beny, "Cross-platform programming model for
+ * many-core lattice Boltzmann simulation", arXiv:2010.11751.
+ *   - one time iteration = collision f_out = Omega(f) followed by streaming
+ *     f_k(x + c_k, t+1) = f_out_k(x, t)  (Section 2.1, collision/streaming eqs.)
+ *   - walls: link-wise bounce-back with momentum exchange,
+ *     f_kbar(x, t+1) = f_out_k(x, t) - 6 t_k rho_w c_k.u_w, rho_w = 1
+ *     (Section 2.1, momentum-exchange equation)
+ *   - memory-access schemes: double population, swap, AA-pattern
+ *     (Section 2.3, Table 1) and the esoteric twist (Geier & Schoenherr 2017)
+ *   - layouts: structure-of-arrays pop[Q][N], array-of-structures pop[N][Q]
+ *     (Section 2.3, end)
+ *   - collision models of Section 2.2 / Section 2.6.
+ *
+ * Conventions common to every call
+ *   - Every function returns LBM_OK (0) or a negative LBM_ERR_* code; the
+ *     text of the last error of the calling thread is lbm_last_error().
+ *   - Cell index i = (x*ny + y)*nz + z (z fastest), N = nx*ny*nz.
+ *   - Canonical population order k = 0..Q-1: the velocities whose first
+ *     non-zero component is -1, sorted by |c|^2 then lexicographically
+ *     (-1 < 0 < 1); then the rest velocity; then the negated first half.
+ *     opposite(k) = k + (Q+1)/2 for k < (Q-1)/2.  For D3Q19 this gives
+ *     c_0 = (-1,0,0) = -c_10 as in Section 2.6.
+ *   - Canonical population arrays are FP64, [Q][N] (SoA), independent of the
+ *     handle's scheme, layout, precision and time-step parity.
+ *   - Flag field: uint8 per cell; 0 = fluid, 1 = resting bounce-back wall,
+ *     2..7 = moving wall with the velocity set by lbm_set_wall_velocity.
+ *     The box is periodic in every axis; closed domains carry explicit wall
+ *     layers.  Solid cells read back as f = 0, rho = 1, u = wall velocity.
+ *   - Pointer arguments marked "host or device" may point to host memory
+ *     (pageable or pinned) or to device memory of the handle's GPU; the
+ *     library detects which with cudaPointerGetAttributes.  Host transfers
+ *     are synchronous with respect to the handle's stream.
+ *   - All device work is enqueued on the handle's stream (default: the legacy
+ *     default stream).  lbm_step does not synchronise.  Handles are not
+ *     thread-safe: one host thread at a time per handle.
+ *   - The library owns every device buffer it allocates; caller buffers stay
+ *     the caller's.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+/* ---- status codes ---- */
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1) /* bad enum, bad size, NULL pointer, n < 0 */
+#define LBM_ERR_OOM (-2)         /* request does not fit in free device memory */
+#define LBM_ERR_STATE (-3)       /* call not allowed in the handle's current state */
+#define LBM_ERR_DIVERGED (-4)    /* non-finite mass or energy detected */
+#define LBM_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define LBM_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+#define LBM_ERR_UNSUPPORTED (-7) /* combination not built (see lbm_supported) */
+
+/* ---- lattices ---- */
+#define LBM_D3Q19 19
+#define LBM_D3Q27 27
+
+/* ---- memory-access schemes (Section 2.3, Table 1) ---- */
+#define LBM_TWOPOP 0   /* double population: read pop, write out at x+c_k; swap arrays */
+#define LBM_SWAP 1     /* collide (store to opposite slot), then 9 (13) pairwise swaps */
+#define LBM_AA 2       /* AA-pattern: local step / pull-collide-push step, alternating */
+#define LBM_ESOTWIST 3 /* esoteric twist: one in-place kernel, slot labels swap each step */
+
+/* ---- collision models (Section 2.2) ---- */
+#define LBM_BGK_W2 0  /* BGK, second-order weighted equilibrium (Section 2.6) */
+#define LBM_BGK_NW4 1 /* BGK, non-weighted product-Maxwellian equilibrium */
+#define LBM_TRT 2     /* two-relaxation-time, magic parameter Lambda */
+#define LBM_REG 3     /* regularized (second-order Hermite projection) */
+#define LBM_RR 4      /* recursive regularized, Hermite-moment form */
+#define LBM_RM 5      /* raw-moment multi-relaxation (Section 2.6 relaxation law) */
+#define LBM_HM 6      /* Hermite-moment multi-relaxation */
+#define LBM_CM 7      /* central-moment multi-relaxation */
+#define LBM_CHM 8     /* central-Hermite-moment multi-relaxation */
+#define LBM_K 9       /* cumulant */
+
+/* ---- layouts (Section 2.3) ---- */
+#define LBM_SOA 0 /* pop[Q][N] */
+#define LBM_AOS 1 /* pop[N][Q] */
+
+/* ---- storage precision ---- */
+#define LBM_F64 0 /* populations f stored in FP64, FP64 arithmetic */
+#define LBM_F32 1 /* shifted populations f - t_k stored in FP32, FP32 arithmetic */
+#define LBM_F16 2 /* shifted populations f - t_k stored in FP16, FP32 arithmetic */
+
+/* ---- relaxation parameters (Section 2.6) ---- */
+#define LBM_PARAM_OMEGA 0      /* omega_nu, shear rate; nu = (1/omega - 1/2)/3 */
+#define LBM_PARAM_OMEGA_BULK 1 /* omega_nu_b of the bulk coupling; default: follows omega */
+#define LBM_PARAM_OMEGA_HIGH 2 /* rate of moments of order >= 3; default 1 */
+#define LBM_PARAM_TRT_LAMBDA 3 /* TRT magic parameter; default 1/4 */
+
+typedef struct lbm_s* lbm_t;
+
+/* Create a lattice.  lattice: 19 or 27; nx, ny, nz >= 1 with N < 2^31;
+ * scheme: LBM_TWOPOP..LBM_ESOTWIST; collision: LBM_BGK_W2..LBM_K;
+ * omega in (0, 2); flags: host array of N bytes (copied).  Layout SoA and
+ * precision FP64 unless changed before the populations are first written.
+ * Device memory for the populations is reserved at the first call that
+ * writes them; LBM_ERR_OOM if it would not fit. */
+LBM_API int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int collision, double omega,
+               const uint8_t* flags);
+
+/* Change layout / precision.  Only before populations are first written
+ * (lbm_init_equilibrium, lbm_set_populations or lbm_step), else LBM_ERR_STATE.
+ * LBM_ERR_UNSUPPORTED for combinations that are not built (see lbm_supported). */
+LBM_API int lbm_set_layout(lbm_t h, int layout);
+LBM_API int lbm_set_precision(lbm_t h, int precision);
+
+/* Velocity of moving-wall kind flag (2..7); rho_w = 1.  Takes effect at the
+ * next step. */
+LBM_API int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, double uz);
+
+/* Set LBM_PARAM_*.  omega and omega_bulk in (0, 2), omega_high in (0, 2],
+ * lambda > 0.  Takes effect at the next step. */
+LBM_API int lbm_set_param(lbm_t h, int key, double value);
+
+/* All device work of this handle goes to this cudaStream_t (NULL: legacy default). */
+LBM_API int lbm_set_stream(lbm_t h, void* stream);
+
+/* f = the collision model's own equilibrium of (rho, u) on every fluid cell.
+ * rho: N doubles, u: 3*N doubles (ux[N], uy[N], uz[N]); host or device.
+ * Either may be NULL: rho = 1, u = 0.  Resets the time-step parity. */
+LBM_API int lbm_init_equilibrium(lbm_t h, const double* rho, const double* u);
+
+/* Enqueue n >= 0 time iterations on the handle's stream; asynchronous.  If
+ * the populations were never written, they are first set to the equilibrium
+ * at rho = 1, u = 0. */
+LBM_API int lbm_step(lbm_t h, int n);
+
+/* rho[N] and u[3*N] (FP64) of the current pre-collision state; host or device.
+ * Either may be NULL.  Synchronises the handle's stream for host outputs. */
+LBM_API int lbm_macroscopic(lbm_t h, double* rho, double* u);
+
+/* Canonical populations f[Q*N] (FP64, [Q][N]); host or device.  Shifted
+ * storage is un-shifted (f = stored + t_k).  Solid cells read 0. */
+LBM_API int lbm_get_populations(lbm_t h, double* f);
+
+/* Load canonical populations f[Q*N]; host or device.  Solid-cell entries are
+ * ignored.  Resets the time-step parity. */
+LBM_API int lbm_set_populations(lbm_t h, const double* f);
+
+/* FP64 sums over fluid cells: mass = sum rho, energy = sum rho |u|^2 / 2.
+ * Host outputs; synchronises the stream.  LBM_ERR_DIVERGED if either is not
+ * finite (the outputs are still written). */
+LBM_API int lbm_reduce(lbm_t h, double* mass, double* energy);
+
+/* Number of time iterations taken since the populations were last written. */
+LBM_API int lbm_steps_done(lbm_t h, long long* steps);
+
+/* Device bytes the handle holds (populations, flags, tables, scratch). */
+LBM_API int lbm_device_bytes(lbm_t h, size_t* bytes);
+
+/* Algorithmic bytes moved per cell update by the handle's step (populations
+ * read + written + the 1-byte cell flag), for roofline accounting. */
+LBM_API int lbm_bytes_per_cell_update(lbm_t h, double* bytes);
+
+/* Free everything the handle owns.  NULL is accepted. */
+LBM_API int lbm_destroy(lbm_t h);
+
+/* 1 if (lattice, scheme, collision, layout, precision) is built, else 0. */
+LBM_API int lbm_supported(int lattice, int scheme, int collision, int layout, int precision);
+
+/* Text of the calling thread's last error ("" if none). */
+LBM_API const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -749,3 +749,21 @@ EXPORT int orc_conserved(int Q, int64_t N, const uint8_t* flags, const double* f
     *energy = e;
     return 0;
 }
+
+/* f = the model's own equilibrium of rho[N], u[3][N] on every fluid cell
+ * (rho or u may be NULL: rho = 1, u = 0); solid cells get 0.  A whole-field
+ * loop of orc_model_equilibrium, for initialising large lattices. */
+EXPORT int orc_init_equilibrium_field(int Q, int model, int64_t N, const uint8_t* flags, const double* rho,
+                                      const double* u, double* f) {
+    const lat_t* L = get_lat(Q);
+    if (!L) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        double fe[ORC_MAXQ] = {0};
+        if (flags[i] == 0) {
+            double uu[3] = {u ? u[i] : 0.0, u ? u[N + i] : 0.0, u ? u[2 * N + i] : 0.0};
+            if (orc_model_equilibrium(Q, model, rho ? rho[i] : 1.0, uu, fe) != 0) return -1;
+        }
+        for (int k = 0; k < Q; ++k) f[(int64_t)k * N + i] = fe[k];
+    }
+    return 0;
+}

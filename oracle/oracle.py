@@ -36,6 +36,7 @@ def lib():
         L.orc_run.argtypes = [ctypes.c_int] * 4 + [u8p, dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, dp]
         L.orc_macroscopic.argtypes = [ctypes.c_int, ctypes.c_int64, u8p, dp, dp, dp, dp]
         L.orc_conserved.argtypes = [ctypes.c_int, ctypes.c_int64, u8p, dp, dp, dp]
+        L.orc_init_equilibrium_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, u8p, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -122,14 +123,19 @@ class Lattice:
         self.wall_u = _c64(wall_table(wall_velocities))
         self.f = np.zeros((Q, self.N))
 
-    def init_equilibrium(self, rho, u):
-        """f = the model's own equilibrium of per-cell rho[N], u[3][N]; solid cells stay 0."""
-        rho = np.broadcast_to(np.asarray(rho, dtype=np.float64), (self.N,))
-        u = np.asarray(u, dtype=np.float64).reshape(3, self.N)
-        self.f[:] = 0.0
-        for i in range(self.N):
-            if self.flags[i] == 0:
-                self.f[:, i] = model_equilibrium(self.Q, self.model, rho[i], u[:, i])
+    def init_equilibrium(self, rho=None, u=None):
+        """f = the model's own equilibrium of per-cell rho[N], u[3][N] (None: rho = 1, u = 0);
+        solid cells get 0."""
+        rp = up = None
+        if rho is not None:
+            rho = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (self.N,)))
+            rp = _dp(rho)
+        if u is not None:
+            u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(3, self.N))
+            up = _dp(u)
+        _check(lib().orc_init_equilibrium_field(self.Q, MODELS[self.model], self.N,
+                                                self.flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                                rp, up, _dp(self.f)), "init_equilibrium")
 
     def step(self, n=1, force=None, perm=None, nthreads=1):
         L = lib()

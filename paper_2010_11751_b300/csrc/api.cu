@@ -1,0 +1,504 @@
+// api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// A handle owns its device buffers (classified flags, one or two population
+// arrays, the wall-term table, reduction partials and a staging buffer for
+// host transfers) and enqueues every kernel on its stream.  The time-step
+// parity and, for the two-population scheme, the current array are host
+// state; step kernels are looked up once per (model, lattice, precision,
+// layout, step kind) from the compiled tables.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "lbm.h"
+
+using namespace lbm;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+size_t elem_size(int prec) { return prec == F64 ? 8 : (prec == F32 ? 4 : 2); }
+
+template <int Q>
+void fill_wall_table(const double (&wall_u)[8][3], double* out) {
+  // W[kind][k] = -6 t_k rho_w c_k.u_w(kind), rho_w = 1 (Section 2.1)
+  for (int fl = 0; fl < 8; ++fl)
+    for (int k = 0; k < Q; ++k) {
+      const double cu = Lat<Q>::c(k, 0) * wall_u[fl][0] + Lat<Q>::c(k, 1) * wall_u[fl][1] +
+                        Lat<Q>::c(k, 2) * wall_u[fl][2];
+      out[fl * Q + k] = fl <= 1 ? 0.0 : -6.0 * Lat<Q>::w(k) * 1.0 * cu;
+    }
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+struct lbm_s {
+  int Q = 19, nx = 0, ny = 0, nz = 0, N = 0;
+  int scheme = LBM_TWOPOP, model = BGK_W2, layout = SOA, prec = F64;
+  double omega = 1.0, omega_bulk = 1.0, omega_high = 1.0, lambda = 0.25;
+  bool bulk_follows = true;
+  double wall_u[8][3] = {};
+  double wall_table[8 * 27] = {};
+  cudaStream_t stream = nullptr;
+  uint8_t* d_flags = nullptr;
+  void* d_pop[2] = {nullptr, nullptr};
+  int npop = 1;
+  int cur = 0;
+  long long steps = 0;
+  bool populated = false;
+  double* d_wall = nullptr;   // [8][Q] wall terms
+  double* d_wallu = nullptr;  // [8][3] wall velocities
+  bool wall_dirty = true;
+  double* d_partials = nullptr;
+  int partials = 0;
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  int threads = 256;
+  StepFn fns[NUM_STEP_KINDS] = {};
+};
+
+namespace {
+
+size_t pop_bytes(const lbm_s* h) { return (size_t)h->Q * (size_t)h->N * elem_size(h->prec); }
+
+int resolve_kernels(lbm_s* h) {
+  for (int sk = 0; sk < NUM_STEP_KINDS; ++sk) h->fns[sk] = step_fn(h->model, h->Q, h->prec, h->layout, sk);
+  if (!h->fns[K_TWOPOP]) return fail(LBM_ERR_UNSUPPORTED, "combination of lattice, model, precision and layout is not built");
+  return LBM_OK;
+}
+
+int ensure_alloc(lbm_s* h) {
+  if (h->d_pop[0]) return LBM_OK;
+  const size_t need = pop_bytes(h) * (size_t)h->npop;
+  size_t freeb = 0, total = 0;
+  LBM_CUDA(cudaMemGetInfo(&freeb, &total));
+  if (need + (size_t(256) << 20) > freeb)
+    return fail(LBM_ERR_OOM, "populations need " + std::to_string(need >> 20) + " MiB, " +
+                                 std::to_string(freeb >> 20) + " MiB free");
+  for (int a = 0; a < h->npop; ++a) {
+    LBM_CUDA(cudaMalloc(&h->d_pop[a], pop_bytes(h)));
+    LBM_CUDA(cudaMemsetAsync(h->d_pop[a], 0, pop_bytes(h), h->stream));
+  }
+  return LBM_OK;
+}
+
+int ensure_stage(lbm_s* h, size_t bytes) {
+  if (h->stage_bytes >= bytes) return LBM_OK;
+  if (h->d_stage) {
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    LBM_CUDA(cudaFree(h->d_stage));
+    h->d_stage = nullptr;
+    h->stage_bytes = 0;
+  }
+  LBM_CUDA(cudaMalloc(&h->d_stage, bytes));
+  h->stage_bytes = bytes;
+  return LBM_OK;
+}
+
+int upload_wall(lbm_s* h) {
+  if (!h->wall_dirty) return LBM_OK;
+  if (h->Q == 19) fill_wall_table<19>(h->wall_u, h->wall_table);
+  else fill_wall_table<27>(h->wall_u, h->wall_table);
+  LBM_CUDA(cudaMemcpyAsync(h->d_wall, h->wall_table, sizeof(double) * 8 * h->Q, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(h->d_wallu, h->wall_u, sizeof(double) * 24, cudaMemcpyHostToDevice, h->stream));
+  // the host tables are members of the handle and outlive the copies
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  h->wall_dirty = false;
+  return LBM_OK;
+}
+
+KArgs make_args(const lbm_s* h) {
+  KArgs a;
+  a.a = h->d_pop[h->cur];
+  a.b = h->npop > 1 ? h->d_pop[1 - h->cur] : nullptr;
+  a.flags = h->d_flags;
+  a.wall = h->d_wall;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
+  a.N = h->N;
+  a.parity = (int)(h->steps & 1);
+  const double w = h->omega, wb = h->bulk_follows ? h->omega : h->omega_bulk;
+  a.omega = w;
+  a.omc = 1.0 - w;
+  a.wminus = (wb - w) / 3.0;
+  a.wplus = a.wminus + w;
+  a.omega_high = h->omega_high;
+  a.trt_minus = 1.0 / (0.5 + h->lambda / (1.0 / w - 0.5));
+  return a;
+}
+
+int load_kind(const lbm_s* h) {
+  const bool odd = (h->steps & 1) != 0;
+  switch (h->scheme) {
+    case LBM_AA: return odd ? LD_AA_ODD : LD_LOCAL;
+    case LBM_ESOTWIST: return odd ? LD_ET_ODD : LD_ET_EVEN;
+    default: return LD_LOCAL;
+  }
+}
+
+int store_kind(const lbm_s* h) { return h->scheme == LBM_ESOTWIST ? LD_ET_EVEN : LD_LOCAL; }
+
+bool nw4_equilibrium(int model) { return !(model == BGK_W2 || model == TRT || model == REG); }
+
+int reset_populations(lbm_s* h) {
+  int rc = ensure_alloc(h);
+  if (rc) return rc;
+  h->cur = 0;
+  h->steps = 0;
+  for (int a = 0; a < h->npop; ++a) LBM_CUDA(cudaMemsetAsync(h->d_pop[a], 0, pop_bytes(h), h->stream));
+  return upload_wall(h);
+}
+
+int init_eq_device(lbm_s* h, const double* rho, const double* u) {
+  int rc = reset_populations(h);
+  if (rc) return rc;
+  KArgs a = make_args(h);
+  LBM_CUDA(launch_init(h->Q, h->prec, h->layout, store_kind(h), nw4_equilibrium(h->model), a, rho, u, h->stream));
+  h->populated = true;
+  return LBM_OK;
+}
+
+int valid_omega(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_supported(int lattice, int scheme, int collision, int layout, int precision) {
+  if (lattice != 19 && lattice != 27) return 0;
+  if (scheme < LBM_TWOPOP || scheme > LBM_ESOTWIST) return 0;
+  if (collision < 0 || collision >= NUM_MODELS) return 0;
+  if (layout != LBM_SOA && layout != LBM_AOS) return 0;
+  if (precision < LBM_F64 || precision > LBM_F16) return 0;
+  return step_fn(collision, lattice, precision, layout, K_TWOPOP) != nullptr ? 1 : 0;
+}
+
+int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int collision, double omega,
+               const uint8_t* flags) {
+  if (!out) return fail(LBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (lattice != 19 && lattice != 27) return fail(LBM_ERR_INVALID_ARG, "lattice must be 19 or 27");
+  if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_ERR_INVALID_ARG, "dimensions must be >= 1");
+  const long long N = (long long)nx * ny * nz;
+  if (N >= (1ll << 31)) return fail(LBM_ERR_INVALID_ARG, "nx*ny*nz must be < 2^31");
+  if (scheme < LBM_TWOPOP || scheme > LBM_ESOTWIST) return fail(LBM_ERR_INVALID_ARG, "unknown scheme");
+  if (collision < 0 || collision >= NUM_MODELS) return fail(LBM_ERR_INVALID_ARG, "unknown collision model");
+  if (!valid_omega(omega)) return fail(LBM_ERR_INVALID_ARG, "omega must be in (0, 2)");
+  if (!flags) return fail(LBM_ERR_INVALID_ARG, "flags is NULL");
+  for (long long i = 0; i < N; ++i)
+    if (flags[i] > 7) return fail(LBM_ERR_INVALID_ARG, "flag values must be 0..7");
+
+  lbm_s* h = new lbm_s();
+  h->Q = lattice;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->N = (int)N;
+  h->scheme = scheme;
+  h->model = collision;
+  h->omega = omega;
+  h->npop = scheme == LBM_TWOPOP ? 2 : 1;
+  int rc = resolve_kernels(h);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  uint8_t* raw = nullptr;
+  cudaError_t e = cudaMalloc(&h->d_flags, N);
+  if (e == cudaSuccess) e = cudaMalloc(&raw, N);
+  if (e == cudaSuccess) e = cudaMemcpy(raw, flags, N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_classify(lattice, raw, h->d_flags, nx, ny, nz, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (raw) cudaFree(raw);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_wall, sizeof(double) * 8 * 27);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_wallu, sizeof(double) * 24);
+  if (e == cudaSuccess) {
+    h->partials = reduce_partials_count(h->N);
+    e = cudaMalloc(&h->d_partials, sizeof(double) * (2 * h->partials + 2));
+  }
+  if (e != cudaSuccess) {
+    lbm_destroy(h);
+    return cuda_fail(e, "lbm_create");
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_set_layout(lbm_t h, int layout) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (layout != LBM_SOA && layout != LBM_AOS) return fail(LBM_ERR_INVALID_ARG, "unknown layout");
+  if (h->populated) return fail(LBM_ERR_STATE, "layout can only change before populations are written");
+  if (!lbm_supported(h->Q, h->scheme, h->model, layout, h->prec))
+    return fail(LBM_ERR_UNSUPPORTED, "layout not built for this precision (AoS is FP64 only)");
+  for (int a = 0; a < 2; ++a)
+    if (h->d_pop[a]) {
+      cudaFree(h->d_pop[a]);
+      h->d_pop[a] = nullptr;
+    }
+  h->layout = layout;
+  return resolve_kernels(h);
+}
+
+int lbm_set_precision(lbm_t h, int precision) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (precision < LBM_F64 || precision > LBM_F16) return fail(LBM_ERR_INVALID_ARG, "unknown precision");
+  if (h->populated) return fail(LBM_ERR_STATE, "precision can only change before populations are written");
+  if (!lbm_supported(h->Q, h->scheme, h->model, h->layout, precision))
+    return fail(LBM_ERR_UNSUPPORTED, "precision not built for this layout (FP32/FP16 are SoA only)");
+  for (int a = 0; a < 2; ++a)
+    if (h->d_pop[a]) {
+      cudaFree(h->d_pop[a]);
+      h->d_pop[a] = nullptr;
+    }
+  h->prec = precision;
+  return resolve_kernels(h);
+}
+
+int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, double uz) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (flag < 2 || flag > 7) return fail(LBM_ERR_INVALID_ARG, "moving-wall flags are 2..7");
+  if (!std::isfinite(ux) || !std::isfinite(uy) || !std::isfinite(uz))
+    return fail(LBM_ERR_INVALID_ARG, "wall velocity must be finite");
+  h->wall_u[flag][0] = ux;
+  h->wall_u[flag][1] = uy;
+  h->wall_u[flag][2] = uz;
+  h->wall_dirty = true;
+  return LBM_OK;
+}
+
+int lbm_set_param(lbm_t h, int key, double v) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  switch (key) {
+    case LBM_PARAM_OMEGA:
+      if (!valid_omega(v)) return fail(LBM_ERR_INVALID_ARG, "omega must be in (0, 2)");
+      h->omega = v;
+      return LBM_OK;
+    case LBM_PARAM_OMEGA_BULK:
+      if (!valid_omega(v)) return fail(LBM_ERR_INVALID_ARG, "omega_bulk must be in (0, 2)");
+      h->omega_bulk = v;
+      h->bulk_follows = false;
+      return LBM_OK;
+    case LBM_PARAM_OMEGA_HIGH:
+      if (!(std::isfinite(v) && v > 0.0 && v <= 2.0)) return fail(LBM_ERR_INVALID_ARG, "omega_high must be in (0, 2]");
+      h->omega_high = v;
+      return LBM_OK;
+    case LBM_PARAM_TRT_LAMBDA:
+      if (!(std::isfinite(v) && v > 0.0)) return fail(LBM_ERR_INVALID_ARG, "lambda must be > 0");
+      h->lambda = v;
+      return LBM_OK;
+    default:
+      return fail(LBM_ERR_INVALID_ARG, "unknown parameter key");
+  }
+}
+
+int lbm_set_stream(lbm_t h, void* stream) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  h->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_t h, const double* rho, const double* u) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  const size_t N = (size_t)h->N;
+  const bool dev_r = !rho || is_device_pointer(rho), dev_u = !u || is_device_pointer(u);
+  if (dev_r && dev_u) return init_eq_device(h, rho, u);
+  int rc = ensure_stage(h, sizeof(double) * 4 * N);
+  if (rc) return rc;
+  double* st = (double*)h->d_stage;
+  const double* dr = rho;
+  const double* du = u;
+  if (rho && !dev_r) {
+    LBM_CUDA(cudaMemcpyAsync(st, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    dr = st;
+  }
+  if (u && !dev_u) {
+    LBM_CUDA(cudaMemcpyAsync(st + N, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+    du = st + N;
+  }
+  return init_eq_device(h, dr, du);
+}
+
+int lbm_step(lbm_t h, int n) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
+  if (!h->populated) {
+    int rc = init_eq_device(h, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  int rc = upload_wall(h);
+  if (rc) return rc;
+  for (int s = 0; s < n; ++s) {
+    KArgs a = make_args(h);
+    cudaError_t e = cudaSuccess;
+    switch (h->scheme) {
+      case LBM_TWOPOP:
+        e = h->fns[K_TWOPOP](a, h->threads, h->stream);
+        h->cur ^= 1;
+        break;
+      case LBM_AA:
+        e = h->fns[(h->steps & 1) ? K_AA_ODD : K_AA_EVEN](a, h->threads, h->stream);
+        break;
+      case LBM_SWAP:
+        e = h->fns[K_AA_EVEN](a, h->threads, h->stream);
+        if (e == cudaSuccess) e = launch_swap_stream(h->Q, h->prec, h->layout, a, h->threads, h->stream);
+        break;
+      case LBM_ESOTWIST:
+        e = h->fns[K_ESOTWIST](a, h->threads, h->stream);
+        break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    ++h->steps;
+  }
+  return LBM_OK;
+}
+
+int lbm_macroscopic(lbm_t h, double* rho, double* u) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->populated) return fail(LBM_ERR_STATE, "populations were never written");
+  int rc = upload_wall(h);
+  if (rc) return rc;
+  const size_t N = (size_t)h->N;
+  const bool dev_r = !rho || is_device_pointer(rho), dev_u = !u || is_device_pointer(u);
+  double* dr = rho;
+  double* du = u;
+  if (!dev_r || !dev_u) {
+    rc = ensure_stage(h, sizeof(double) * 4 * N);
+    if (rc) return rc;
+    if (!dev_r) dr = (double*)h->d_stage;
+    if (!dev_u) du = (double*)h->d_stage + N;
+  }
+  KArgs a = make_args(h);
+  LBM_CUDA(launch_macro(h->Q, h->prec, h->layout, load_kind(h), a, dr, du, h->d_wallu, h->stream));
+  if (!dev_r) LBM_CUDA(cudaMemcpyAsync(rho, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  if (!dev_u) LBM_CUDA(cudaMemcpyAsync(u, du, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+  if (!dev_r || !dev_u) LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_t h, double* f) {
+  if (!h || !f) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->populated) return fail(LBM_ERR_STATE, "populations were never written");
+  const size_t bytes = sizeof(double) * (size_t)h->Q * (size_t)h->N;
+  const bool dev = is_device_pointer(f);
+  double* dst = f;
+  if (!dev) {
+    int rc = ensure_stage(h, bytes);
+    if (rc) return rc;
+    dst = (double*)h->d_stage;
+  }
+  KArgs a = make_args(h);
+  LBM_CUDA(launch_get(h->Q, h->prec, h->layout, load_kind(h), a, dst, h->stream));
+  if (!dev) {
+    LBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_t h, const double* f) {
+  if (!h || !f) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  const size_t bytes = sizeof(double) * (size_t)h->Q * (size_t)h->N;
+  const double* src = f;
+  int rc;
+  if (!is_device_pointer(f)) {
+    rc = ensure_stage(h, bytes);
+    if (rc) return rc;
+    LBM_CUDA(cudaMemcpyAsync(h->d_stage, f, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = (const double*)h->d_stage;
+  }
+  rc = reset_populations(h);
+  if (rc) return rc;
+  KArgs a = make_args(h);
+  LBM_CUDA(launch_set(h->Q, h->prec, h->layout, store_kind(h), a, src, h->stream));
+  h->populated = true;
+  return LBM_OK;
+}
+
+int lbm_reduce(lbm_t h, double* mass, double* energy) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->populated) return fail(LBM_ERR_STATE, "populations were never written");
+  KArgs a = make_args(h);
+  double* out2 = h->d_partials + 2 * h->partials;
+  LBM_CUDA(launch_reduce(h->Q, h->prec, h->layout, load_kind(h), a, h->d_partials, out2, h->stream));
+  double r[2];
+  LBM_CUDA(cudaMemcpyAsync(r, out2, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (mass) *mass = r[0];
+  if (energy) *energy = r[1];
+  if (!std::isfinite(r[0]) || !std::isfinite(r[1])) return fail(LBM_ERR_DIVERGED, "mass or energy is not finite");
+  return LBM_OK;
+}
+
+int lbm_steps_done(lbm_t h, long long* steps) {
+  if (!h || !steps) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  *steps = h->steps;
+  return LBM_OK;
+}
+
+int lbm_device_bytes(lbm_t h, size_t* bytes) {
+  if (!h || !bytes) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  size_t b = (size_t)h->N + sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2) + h->stage_bytes;
+  for (int a = 0; a < 2; ++a)
+    if (h->d_pop[a]) b += pop_bytes(h);
+  *bytes = b;
+  return LBM_OK;
+}
+
+int lbm_bytes_per_cell_update(lbm_t h, double* bytes) {
+  if (!h || !bytes) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  const double pops = (double)h->Q * (double)elem_size(h->prec);
+  // two-population, AA and esoteric twist read and write every population once;
+  // swap reads and writes them twice (collision pass, then streaming pass)
+  *bytes = h->scheme == LBM_SWAP ? 4.0 * pops + 2.0 : 2.0 * pops + 1.0;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_t h) {
+  if (!h) return LBM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (int a = 0; a < 2; ++a)
+    if (h->d_pop[a]) cudaFree(h->d_pop[a]);
+  if (h->d_flags) cudaFree(h->d_flags);
+  if (h->d_wall) cudaFree(h->d_wall);
+  if (h->d_wallu) cudaFree(h->d_wallu);
+  if (h->d_partials) cudaFree(h->d_partials);
+  if (h->d_stage) cudaFree(h->d_stage);
+  delete h;
+  return LBM_OK;
+}
+
+}  // extern "C"

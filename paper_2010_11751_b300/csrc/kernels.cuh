@@ -1,0 +1,269 @@
+// kernels.cuh -- fused stream-and-collide kernels for the four memory-access
+// schemes, plus the state-access kernels (macroscopic fields, canonical
+// get/set, equilibrium initialisation, FP64 conserved sums, swap streaming).
+//
+// One thread per cell, cell index i = (x*ny + y)*nz + z (z fastest, so the
+// Q population streams of the SoA layout are coalesced along z).
+//
+// Schemes (Section 2.3, Table 1 of the paper), with the wall term of the
+// bounce-back rule  f_kbar(x, t+1) = f_out_k(x) - 6 t_k rho_w c_k.u_w
+// (Section 2.1) added at the moment the reflected population is written, so
+// that between steps every scheme stores an exact permutation of the
+// canonical populations:
+//   TWOPOP  read pop_k(x); write out_k(x + c_k), or out_kbar(x) = f_out_k + W_k
+//           if x + c_k is solid.                        (Table 1, row 2Pop)
+//   AA even read pop_k(x); write pop_kbar(x) = f_out_k (+ W_k if x + c_k solid).
+//           The swap scheme's collision pass is this same kernel.
+//   AA odd  read f_k(x) = pop_kbar(x - c_k) if x - c_k is fluid, else pop_k(x);
+//           write pop_k(x + c_k) = f_out_k if fluid, else pop_kbar(x) = f_out_k + W_k.
+//           (Table 1 AA rows; the pull side reads the neighbour in -c_k, the
+//           only reading consistent with the even step's storage rule.)
+//   ESOTWIST (Geier & Schoenherr 2017)  physical slot of label k at parity p:
+//           k (p even) or kbar (p odd).  Read f_k(x) at cell x - max(c_k, 0)
+//           from slot(k) (slot(kbar) if x - c_k is solid); write f_out_k to
+//           slot(kbar) at cell x + min(c_k, 0).  Same kernel every step.
+//   SWAP stream: for the first-half directions k, swap pop_kbar(x) with
+//           pop_k(x + c_k) when both cells are fluid.   (Table 1, row Swap)
+#pragma once
+#include <cuda_runtime.h>
+
+#include "collision.cuh"
+
+namespace lbm {
+
+enum Layout : int { SOA = 0, AOS = 1 };
+enum StepKind : int { K_TWOPOP = 0, K_AA_EVEN = 1, K_AA_ODD = 2, K_ESOTWIST = 3, NUM_STEP_KINDS = 4 };
+// where the canonical pre-collision populations are found
+enum LoadKind : int { LD_LOCAL = 0, LD_AA_ODD = 1, LD_ET_EVEN = 2, LD_ET_ODD = 3, NUM_LOAD_KINDS = 4 };
+
+struct KArgs {
+  void* a;                // populations (current state)
+  void* b;                // destination array of the two-population scheme
+  const uint8_t* flags;   // classified flag bytes
+  const double* wall;     // wall term table [8][Q]: -6 t_k c_k.u_w(kind)
+  int nx, ny, nz, N;
+  int parity;             // time-step parity (esoteric twist slot labels)
+  double omega, omc, wplus, wminus, omega_high, trt_minus;
+};
+
+// ---------------------------------------------------------------------------
+// population addressing
+// ---------------------------------------------------------------------------
+template <int Q, int L>
+__device__ __forceinline__ size_t paddr(int k, int i, int N) {
+  if constexpr (L == SOA) return (size_t)k * (size_t)N + (size_t)i;
+  else return (size_t)i * Q + (size_t)k;
+}
+
+template <int P>
+__device__ __forceinline__ typename Store<P>::R ldp(const void* base, size_t a) {
+  using S = typename Store<P>::S;
+  return Store<P>::to_r(__ldg(reinterpret_cast<const S*>(base) + a));
+}
+template <>
+__device__ __forceinline__ float ldp<F16>(const void* base, size_t a) {
+  return __half2float(reinterpret_cast<const __half*>(base)[a]);
+}
+template <int P>
+__device__ __forceinline__ void stp(void* base, size_t a, typename Store<P>::R v) {
+  using S = typename Store<P>::S;
+  reinterpret_cast<S*>(base)[a] = Store<P>::from_r(v);
+}
+
+// ---------------------------------------------------------------------------
+// neighbour access: FAST = interior bulk cell (no wrap, no solid neighbour)
+// ---------------------------------------------------------------------------
+template <bool FAST>
+struct Nb {
+  int i, x, y, z;
+  int nx, ny, nz, sxy;
+  const uint8_t* flags;
+  __device__ __forceinline__ Nb(int i_, const KArgs& a) : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
+    sxy = a.ny * a.nz;
+    if constexpr (!FAST) {
+      x = i / sxy;
+      const int r = i - x * sxy;
+      y = r / nz;
+      z = r - y * nz;
+    } else {
+      x = y = z = 0;
+    }
+  }
+  // index of the cell at offset (dx, dy, dz), periodic
+  template <int DX, int DY, int DZ>
+  __device__ __forceinline__ int at() const {
+    if constexpr (FAST) {
+      return i + DX * sxy + DY * nz + DZ;
+    } else {
+      int xn = x + DX, yn = y + DY, zn = z + DZ;
+      if constexpr (DX != 0) xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
+      if constexpr (DY != 0) yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
+      if constexpr (DZ != 0) zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
+      return (xn * ny + yn) * nz + zn;
+    }
+  }
+  // wall kind of the neighbour along c_k (0 = fluid)
+  template <int Q, int K>
+  __device__ __forceinline__ int kind() const {
+    if constexpr (FAST) return 0;
+    else return flags[at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>()] & FLAG_KIND;
+  }
+  template <int Q, int K>
+  __device__ __forceinline__ int idx() const {
+    return at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>();
+  }
+};
+
+template <int Q, int K>
+__host__ __device__ constexpr int cpos(int d) { return Lat<Q>::c(K, d) > 0 ? Lat<Q>::c(K, d) : 0; }
+template <int Q, int K>
+__host__ __device__ constexpr int cneg(int d) { return Lat<Q>::c(K, d) < 0 ? Lat<Q>::c(K, d) : 0; }
+
+template <int Q, int K, int PAR>
+__host__ __device__ constexpr int et_slot(bool bounced) {
+  // label K (or its opposite if the population arrives by reflection) at parity PAR
+  return ((PAR == 0) != bounced) ? K : Lat<Q>::opp(K);
+}
+
+// ---------------------------------------------------------------------------
+// canonical load: the pre-collision populations of cell i, for the state kind
+// ---------------------------------------------------------------------------
+template <int Q, int P, int L, int LD, bool FAST, typename T>
+__device__ __forceinline__ void load_cell(const KArgs& a, const Nb<FAST>& nb, const void* pop, T (&f)[Q]) {
+  const int N = a.N;
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    constexpr int kb = Lat<Q>::opp(k);
+    size_t ad;
+    if constexpr (LD == LD_LOCAL || k == Lat<Q>::REST) {
+      ad = paddr<Q, L>(k, nb.i, N);
+    } else if constexpr (LD == LD_AA_ODD) {
+      // f_k(x) = pop_kbar(x - c_k) if x - c_k fluid, else pop_k(x)
+      if (nb.template kind<Q, kb>() == 0) ad = paddr<Q, L>(kb, nb.template idx<Q, kb>(), N);
+      else ad = paddr<Q, L>(k, nb.i, N);
+    } else {
+      constexpr int PAR = LD == LD_ET_EVEN ? 0 : 1;
+      const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
+      if (nb.template kind<Q, kb>() == 0) ad = paddr<Q, L>(et_slot<Q, k, PAR>(false), cell, N);
+      else ad = paddr<Q, L>(et_slot<Q, k, PAR>(true), cell, N);
+    }
+    f[k] = T(ldp<P>(pop, ad));
+  });
+}
+
+// canonical store (inverse of load_cell at parity 0 / local storage)
+template <int Q, int P, int L, int LD, bool FAST>
+__device__ __forceinline__ void store_cell_canonical(const KArgs& a, const Nb<FAST>& nb, void* pop,
+                                                     const typename Store<P>::R (&f)[Q]) {
+  const int N = a.N;
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    constexpr int kb = Lat<Q>::opp(k);
+    size_t ad;
+    if constexpr (LD == LD_LOCAL || k == Lat<Q>::REST) {
+      ad = paddr<Q, L>(k, nb.i, N);
+    } else {
+      const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
+      ad = paddr<Q, L>(et_slot<Q, k, 0>(nb.template kind<Q, kb>() != 0), cell, N);
+    }
+    stp<P>(pop, ad, f[k]);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// the fused stream-and-collide step
+// ---------------------------------------------------------------------------
+template <int Q, int M, int P, int L, int SK, bool FAST>
+__device__ __forceinline__ void step_cell(const KArgs& a, int i) {
+  using R = typename Store<P>::R;
+  constexpr bool SH = Store<P>::shifted;
+  constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : (SK == K_ESOTWIST ? LD_ET_EVEN : LD_LOCAL);
+  const Nb<FAST> nb(i, a);
+  const int N = a.N;
+  R f[Q];
+  if constexpr (SK == K_ESOTWIST) {
+    if (a.parity == 0) load_cell<Q, P, L, LD_ET_EVEN, FAST>(a, nb, a.a, f);
+    else load_cell<Q, P, L, LD_ET_ODD, FAST>(a, nb, a.a, f);
+  } else {
+    load_cell<Q, P, L, LD, FAST>(a, nb, a.a, f);
+  }
+  CP<R> cp;
+  cp.omega = R(a.omega);
+  cp.omc = R(a.omc);
+  cp.wplus = R(a.wplus);
+  cp.wminus = R(a.wminus);
+  cp.omega_high = R(a.omega_high);
+  cp.trt_minus = R(a.trt_minus);
+  collide<Q, M, R, SH>(f, cp);
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    constexpr int kb = Lat<Q>::opp(k);
+    if constexpr (k == Lat<Q>::REST) {
+      if constexpr (SK == K_TWOPOP) stp<P>(a.b, paddr<Q, L>(k, i, N), f[k]);
+      else stp<P>(a.a, paddr<Q, L>(k, i, N), f[k]);
+    } else {
+      const int wk = nb.template kind<Q, k>();
+      R v = f[k];
+      if (!FAST && wk != 0) v = v + R(__ldg(a.wall + wk * Q + k));
+      if constexpr (SK == K_TWOPOP) {
+        if (wk == 0) stp<P>(a.b, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
+        else stp<P>(a.b, paddr<Q, L>(kb, i, N), v);
+      } else if constexpr (SK == K_AA_EVEN) {
+        stp<P>(a.a, paddr<Q, L>(kb, i, N), v);
+      } else if constexpr (SK == K_AA_ODD) {
+        if (wk == 0) stp<P>(a.a, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
+        else stp<P>(a.a, paddr<Q, L>(kb, i, N), v);
+      } else {  // esoteric twist
+        const int cell = nb.template at<cneg<Q, k>(0), cneg<Q, k>(1), cneg<Q, k>(2)>();
+        const int slot = a.parity == 0 ? kb : k;
+        stp<P>(a.a, paddr<Q, L>(slot, cell, N), v);
+      }
+    }
+  });
+}
+
+template <int Q, int M, int P, int L, int SK>
+__global__ void __launch_bounds__(256) step_kernel(KArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const uint8_t fl = a.flags[i];
+  if (fl == 0) step_cell<Q, M, P, L, SK, true>(a, i);
+  else if ((fl & FLAG_KIND) == 0) step_cell<Q, M, P, L, SK, false>(a, i);
+}
+
+using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
+
+template <int Q, int M, int P, int L, int SK>
+cudaError_t launch_step(const KArgs& a, int threads, cudaStream_t s) {
+  const int blocks = (a.N + threads - 1) / threads;
+  step_kernel<Q, M, P, L, SK><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// one model: all lattices, storages, layouts and step kinds
+template <int M>
+StepFn step_fn_for_model(int Q, int P, int L, int SK) {
+#define LBM_SK(QQ, PP, LL)                                      \
+  switch (SK) {                                                 \
+    case K_TWOPOP: return &launch_step<QQ, M, PP, LL, K_TWOPOP>; \
+    case K_AA_EVEN: return &launch_step<QQ, M, PP, LL, K_AA_EVEN>; \
+    case K_AA_ODD: return &launch_step<QQ, M, PP, LL, K_AA_ODD>; \
+    case K_ESOTWIST: return &launch_step<QQ, M, PP, LL, K_ESOTWIST>; \
+    default: return nullptr;                                    \
+  }
+  if (Q == 19) {
+    if (P == F64 && L == SOA) { LBM_SK(19, F64, SOA) }
+    if (P == F64 && L == AOS) { LBM_SK(19, F64, AOS) }
+    if (P == F32 && L == SOA) { LBM_SK(19, F32, SOA) }
+    if (P == F16 && L == SOA) { LBM_SK(19, F16, SOA) }
+  } else if (Q == 27) {
+    if (P == F64 && L == SOA) { LBM_SK(27, F64, SOA) }
+    if (P == F64 && L == AOS) { LBM_SK(27, F64, AOS) }
+    if (P == F32 && L == SOA) { LBM_SK(27, F32, SOA) }
+    if (P == F16 && L == SOA) { LBM_SK(27, F16, SOA) }
+  }
+#undef LBM_SK
+  return nullptr;
+}
+
+}  // namespace lbm

@@ -1,0 +1,9 @@
+// model_k.cu -- step kernels of the KUM collision model for every lattice,
+// storage precision, layout and step kind (one translation unit per model so
+// that the build parallelises).
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace lbm {
+StepFn step_fn_k(int Q, int P, int L, int SK) { return step_fn_for_model<KUM>(Q, P, L, SK); }
+}  // namespace lbm

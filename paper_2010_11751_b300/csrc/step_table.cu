@@ -1,0 +1,32 @@
+// step_table.cu -- model dispatch of the step kernels.
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace lbm {
+StepFn step_fn_bgk_w2(int, int, int, int);
+StepFn step_fn_bgk_nw4(int, int, int, int);
+StepFn step_fn_trt(int, int, int, int);
+StepFn step_fn_reg(int, int, int, int);
+StepFn step_fn_rr(int, int, int, int);
+StepFn step_fn_rm(int, int, int, int);
+StepFn step_fn_hm(int, int, int, int);
+StepFn step_fn_cm(int, int, int, int);
+StepFn step_fn_chm(int, int, int, int);
+StepFn step_fn_k(int, int, int, int);
+
+StepFn step_fn(int model, int Q, int P, int L, int SK) {
+  switch (model) {
+    case BGK_W2: return step_fn_bgk_w2(Q, P, L, SK);
+    case BGK_NW4: return step_fn_bgk_nw4(Q, P, L, SK);
+    case TRT: return step_fn_trt(Q, P, L, SK);
+    case REG: return step_fn_reg(Q, P, L, SK);
+    case RR: return step_fn_rr(Q, P, L, SK);
+    case RM: return step_fn_rm(Q, P, L, SK);
+    case HM: return step_fn_hm(Q, P, L, SK);
+    case CM: return step_fn_cm(Q, P, L, SK);
+    case CHM: return step_fn_chm(Q, P, L, SK);
+    case KUM: return step_fn_k(Q, P, L, SK);
+    default: return nullptr;
+  }
+}
+}  // namespace lbm

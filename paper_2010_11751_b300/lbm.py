@@ -1,0 +1,281 @@
+"""Thin ctypes binding of liblbm.so (the C ABI of include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Module-level functions carry the C names (``lbm_create``,
+``lbm_step``, ...) and raise ``LBMError`` on a non-zero status.  Arrays may be
+numpy arrays (host) or torch tensors (host or CUDA); they must be contiguous
+float64 (populations, fields) or uint8 (flags).  There is no fallback: if the
+library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY = os.path.join(_HERE, "liblbm.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_STATE, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+D3Q19, D3Q27 = 19, 27
+TWOPOP, SWAP, AA, ESOTWIST = 0, 1, 2, 3
+SCHEMES = {"twopop": TWOPOP, "swap": SWAP, "aa": AA, "esotwist": ESOTWIST}
+BGK_W2, BGK_NW4, TRT, REG, RR, RM, HM, CM, CHM, K = range(10)
+MODELS = {"BGK_W2": BGK_W2, "BGK_NW4": BGK_NW4, "TRT": TRT, "REG": REG, "RR": RR, "RM": RM, "HM": HM, "CM": CM,
+          "CHM": CHM, "K": K}
+SOA, AOS = 0, 1
+F64, F32, F16 = 0, 1, 2
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}
+PARAM_OMEGA, PARAM_OMEGA_BULK, PARAM_OMEGA_HIGH, PARAM_TRT_LAMBDA = 0, 1, 2, 3
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBRARY):
+        raise LBMError(ERR_STATE, f"{LIBRARY} is missing; build it with paper_2010_11751_b300.build.build()")
+    L = ctypes.CDLL(LIBRARY)
+    vp, dp, u8p = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+    i, d = ctypes.c_int, ctypes.c_double
+    sigs = {
+        "lbm_create": [ctypes.POINTER(vp), i, i, i, i, i, i, d, u8p],
+        "lbm_set_layout": [vp, i],
+        "lbm_set_precision": [vp, i],
+        "lbm_set_wall_velocity": [vp, i, d, d, d],
+        "lbm_set_param": [vp, i, d],
+        "lbm_set_stream": [vp, vp],
+        "lbm_init_equilibrium": [vp, dp, dp],
+        "lbm_step": [vp, i],
+        "lbm_macroscopic": [vp, dp, dp],
+        "lbm_get_populations": [vp, dp],
+        "lbm_set_populations": [vp, dp],
+        "lbm_reduce": [vp, ctypes.POINTER(d), ctypes.POINTER(d)],
+        "lbm_steps_done": [vp, ctypes.POINTER(ctypes.c_longlong)],
+        "lbm_device_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
+        "lbm_bytes_per_cell_update": [vp, ctypes.POINTER(d)],
+        "lbm_destroy": [vp],
+        "lbm_supported": [i, i, i, i, i],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.lbm_last_error.argtypes = []
+    L.lbm_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        raise LBMError(rc, lib().lbm_last_error().decode())
+    return rc
+
+
+def ptr(a):
+    """Raw address of a numpy array / torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+# ---- C names, marshalling only ----
+def lbm_create(lattice, nx, ny, nz, scheme, collision, omega, flags):
+    h = ctypes.c_void_p()
+    fl = np.ascontiguousarray(flags, dtype=np.uint8)
+    _check(lib().lbm_create(ctypes.byref(h), lattice, nx, ny, nz, scheme, collision, omega, fl.ctypes.data))
+    return h
+
+
+def lbm_set_layout(h, layout):
+    return _check(lib().lbm_set_layout(h, layout))
+
+
+def lbm_set_precision(h, precision):
+    return _check(lib().lbm_set_precision(h, precision))
+
+
+def lbm_set_wall_velocity(h, flag, ux, uy, uz):
+    return _check(lib().lbm_set_wall_velocity(h, flag, ux, uy, uz))
+
+
+def lbm_set_param(h, key, value):
+    return _check(lib().lbm_set_param(h, key, value))
+
+
+def lbm_set_stream(h, stream):
+    return _check(lib().lbm_set_stream(h, stream))
+
+
+def lbm_init_equilibrium(h, rho=None, u=None):
+    return _check(lib().lbm_init_equilibrium(h, ptr(rho), ptr(u)))
+
+
+def lbm_step(h, n):
+    return _check(lib().lbm_step(h, n))
+
+
+def lbm_macroscopic(h, rho, u):
+    return _check(lib().lbm_macroscopic(h, ptr(rho), ptr(u)))
+
+
+def lbm_get_populations(h, f):
+    return _check(lib().lbm_get_populations(h, ptr(f)))
+
+
+def lbm_set_populations(h, f):
+    return _check(lib().lbm_set_populations(h, ptr(f)))
+
+
+def lbm_reduce(h):
+    m, e = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lbm_reduce(h, ctypes.byref(m), ctypes.byref(e)))
+    return m.value, e.value
+
+
+def lbm_steps_done(h):
+    v = ctypes.c_longlong()
+    _check(lib().lbm_steps_done(h, ctypes.byref(v)))
+    return v.value
+
+
+def lbm_device_bytes(h):
+    v = ctypes.c_size_t()
+    _check(lib().lbm_device_bytes(h, ctypes.byref(v)))
+    return v.value
+
+
+def lbm_bytes_per_cell_update(h):
+    v = ctypes.c_double()
+    _check(lib().lbm_bytes_per_cell_update(h, ctypes.byref(v)))
+    return v.value
+
+
+def lbm_destroy(h):
+    return _check(lib().lbm_destroy(h))
+
+
+def lbm_supported(lattice, scheme, collision, layout, precision):
+    return bool(lib().lbm_supported(lattice, scheme, collision, layout, precision))
+
+
+def lbm_last_error():
+    return lib().lbm_last_error().decode()
+
+
+def _enum(v, table):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+class Lattice:
+    """One lattice on the GPU: a handle plus host-side bookkeeping of its sizes."""
+
+    def __init__(self, lattice, nx, ny, nz, scheme, collision, omega, flags, layout=SOA, precision=F64,
+                 wall_velocities=None, omega_bulk=None, omega_high=None, trt_lambda=None, stream=None):
+        self.Q, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        self.h = lbm_create(self.Q, self.nx, self.ny, self.nz, _enum(scheme, SCHEMES), _enum(collision, MODELS),
+                            float(omega), flags)
+        try:
+            if layout != SOA:
+                lbm_set_layout(self.h, layout)
+            if precision != F64:
+                lbm_set_precision(self.h, _enum(precision, PRECISIONS))
+            for fl, v in (wall_velocities or {}).items():
+                lbm_set_wall_velocity(self.h, int(fl), *map(float, v))
+            if omega_bulk is not None:
+                lbm_set_param(self.h, PARAM_OMEGA_BULK, omega_bulk)
+            if omega_high is not None:
+                lbm_set_param(self.h, PARAM_OMEGA_HIGH, omega_high)
+            if trt_lambda is not None:
+                lbm_set_param(self.h, PARAM_TRT_LAMBDA, trt_lambda)
+            if stream is not None:
+                lbm_set_stream(self.h, stream)
+        except Exception:
+            self.close()
+            raise
+
+    def init_equilibrium(self, rho=None, u=None):
+        lbm_init_equilibrium(self.h, rho, u)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def macroscopic(self, rho=None, u=None):
+        """Fills the given buffers (host or device); allocates host numpy arrays if none given."""
+        if rho is None and u is None:
+            rho, u = np.empty(self.N), np.empty(3 * self.N)
+            lbm_macroscopic(self.h, rho, u)
+            return rho, u.reshape(3, self.N)
+        lbm_macroscopic(self.h, rho, u)
+        return rho, u
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.empty(self.Q * self.N)
+            lbm_get_populations(self.h, out)
+            return out.reshape(self.Q, self.N)
+        lbm_get_populations(self.h, out)
+        return out
+
+    def set_populations(self, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        lbm_set_populations(self.h, f)
+
+    def reduce(self):
+        return lbm_reduce(self.h)
+
+    def set_param(self, key, value):
+        lbm_set_param(self.h, key, value)
+
+    @property
+    def steps_done(self):
+        return lbm_steps_done(self.h)
+
+    @property
+    def bytes_per_cell_update(self):
+        return lbm_bytes_per_cell_update(self.h)
+
+    @property
+    def device_bytes(self):
+        return lbm_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

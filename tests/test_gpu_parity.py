@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle.
+
+* every collision model on D3Q19 and D3Q27, two-population SoA FP64, element by element,
+  within 1e-12 relative per population, on a lattice that spans several thread blocks with a
+  ragged tail, random walls of three kinds and periodic wrap;
+* every scheme (swap, AA, esoteric twist) and the AoS layout bit-identical to the
+  two-population scheme after odd and even step counts (the six strategies of Section 2.3
+  compute the same map);
+* macroscopic fields, conserved sums and the equilibrium initialisation against the oracle;
+* the 32^3 cavity (BGK-W2, two-population SoA, Re 100, 100 steps) element by element;
+* degenerate sizes, checkpoint/resume across parities, host and device buffers.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import MODELS, RTOL_F64, SCHEMES, WALLS, case, gpu_lattice, gpu_run, oracle_run, prm, rel_err
+from oracle import oracle as O
+from paper_2010_11751_b300 import inputs as I
+from paper_2010_11751_b300 import lbm as L
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (10, 9, 12)  # 1080 cells: five 256-thread blocks, the last one ragged
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("model", MODELS)
+def test_twopop_matches_oracle(Q, model):
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=11, model=model)
+    ref = oracle_run(Q, DIMS, flags, model, p, f0, 6)
+    got = gpu_run(Q, DIMS, flags, model, p, f0, 6)
+    assert rel_err(got, ref.f, flags) <= RTOL_F64
+    assert np.all(got[:, flags != 0] == 0.0)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("model", MODELS)
+def test_schemes_and_layouts_bit_identical(Q, model):
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=21, model=model)
+    for steps in (5, 6):
+        base = gpu_run(Q, DIMS, flags, model, p, f0, steps)
+        for name in ("swap", "aa", "esotwist"):
+            for layout in (L.SOA, L.AOS):
+                got = gpu_run(Q, DIMS, flags, model, p, f0, steps, scheme=name, layout=layout)
+                assert np.array_equal(got, base), (name, layout, steps)
+        got = gpu_run(Q, DIMS, flags, model, p, f0, steps, scheme="twopop", layout=L.AOS)
+        assert np.array_equal(got, base)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_macroscopic_and_conserved_sums(Q, scheme):
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=31)
+    for steps in (3, 4):
+        ref = oracle_run(Q, DIMS, flags, "TRT", p, f0, steps)
+        rho_o, u_o = ref.macroscopic()
+        m_o, e_o = ref.conserved()
+        with gpu_lattice(Q, DIMS, flags, "TRT", p, scheme) as g:
+            g.set_populations(f0)
+            g.step(steps)
+            rho, u = g.macroscopic()
+            m, e = g.reduce()
+        assert np.max(np.abs(rho - rho_o) / rho_o) < 1e-13
+        assert np.max(np.abs(u - u_o)) < 1e-13
+        assert abs(m - m_o) <= 1e-13 * m_o
+        assert abs(e - e_o) <= 1e-10 * e_o
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("model", ["BGK_W2", "BGK_NW4", "K"])
+@pytest.mark.parametrize("scheme", ["twopop", "esotwist"])
+def test_init_equilibrium(Q, model, scheme):
+    nx, ny, nz = DIMS
+    flags = I.random_obstacle_flags(nx, ny, nz, 0.1, seed=41)
+    rho, u = I.smooth_random_fields(nx, ny, nz, amp=0.05, seed=42)
+    ref = O.Lattice(Q, nx, ny, nz, flags, model, O.params(1.0), WALLS)
+    ref.init_equilibrium(rho, u)
+    with gpu_lattice(Q, DIMS, flags, model, prm(), scheme) as g:
+        g.init_equilibrium(np.ascontiguousarray(rho), np.ascontiguousarray(u))
+        got = g.get_populations()
+    assert rel_err(got, ref.f, flags) < 1e-14
+
+
+def test_cavity_32_bgk_twopop_100_steps():
+    n = 32
+    flags = I.cavity_flags(n, n, n)
+    nu = I.cavity_nu(0.02, n, 100.0)
+    omega = 1.0 / (3.0 * nu + 0.5)
+    ref = O.Lattice(19, n, n, n, flags, "BGK_W2", O.params(omega), {I.LID: (0.02, 0.0, 0.0)})
+    ref.init_equilibrium(1.0, np.zeros((3, n ** 3)))
+    ref.step(100)
+    with L.Lattice(19, n, n, n, "twopop", "BGK_W2", omega, flags, wall_velocities={I.LID: (0.02, 0.0, 0.0)}) as g:
+        g.init_equilibrium()
+        g.step(100)
+        got = g.get_populations()
+        m, _ = g.reduce()
+    assert rel_err(got, ref.f, flags) <= RTOL_F64
+    m0 = float((flags == 0).sum())
+    assert abs(m - m0) <= 1e-12 * m0
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 5, 7), (2, 3, 4), (3, 3, 3), (5, 1, 2), (7, 6, 5)])
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_degenerate_and_tiny_sizes(dims, scheme):
+    Q, model, p = 19, "K", prm()
+    nx, ny, nz = dims
+    flags = I.random_obstacle_flags(nx, ny, nz, 0.2 if nx * ny * nz > 8 else 0.0, seed=51)
+    rho, u = I.smooth_random_fields(nx, ny, nz, seed=52)
+    ref0 = O.Lattice(Q, nx, ny, nz, flags, model, O.params(1.0), WALLS)
+    ref0.init_equilibrium(rho, u)
+    f0 = ref0.f * I.noise(ref0.f.shape, 0.05, seed=53)
+    ref = oracle_run(Q, dims, flags, model, p, f0, 5)
+    got = gpu_run(Q, dims, flags, model, p, f0, 5, scheme=scheme)
+    if (flags == 0).any():
+        assert rel_err(got, ref.f, flags) <= RTOL_F64
+
+
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_all_solid_lattice(scheme):
+    flags = np.ones(4 * 4 * 4, np.uint8)
+    with L.Lattice(27, 4, 4, 4, scheme, "BGK_W2", 1.2, flags) as g:
+        g.init_equilibrium()
+        g.step(3)
+        m, e = g.reduce()
+        rho, u = g.macroscopic()
+    assert m == 0.0 and e == 0.0
+    assert np.all(rho == 1.0) and np.all(u == 0.0)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_checkpoint_resume_bit_identical(Q, scheme):
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=61)
+    full = gpu_run(Q, DIMS, flags, "RR", p, f0, 7, scheme=scheme)
+    with gpu_lattice(Q, DIMS, flags, "RR", p, scheme) as g:
+        g.set_populations(f0)
+        g.step(3)  # odd parity for AA and the esoteric twist
+        mid = g.get_populations().copy()
+    resumed = gpu_run(Q, DIMS, flags, "RR", p, mid, 4, scheme=scheme)
+    assert np.array_equal(full, resumed)
+
+
+def test_host_and_device_buffers_agree():
+    torch = pytest.importorskip("torch")
+    Q, p = 19, prm()
+    flags, f0 = case(Q, DIMS, seed=71)
+    with gpu_lattice(Q, DIMS, flags, "CM", p, "aa") as g:
+        g.set_populations(torch.from_numpy(f0.ravel().copy()).cuda())
+        g.step(3)
+        fd = torch.empty(Q * g.N, dtype=torch.float64, device="cuda")
+        g.get_populations(fd)
+        rd = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        ud = torch.empty(3 * g.N, dtype=torch.float64, device="cuda")
+        g.macroscopic(rd, ud)
+        torch.cuda.synchronize()
+        fh = g.get_populations()
+        rh, uh = g.macroscopic()
+    assert np.array_equal(fd.cpu().numpy().reshape(Q, -1), fh)
+    assert np.array_equal(rd.cpu().numpy(), rh) and np.array_equal(ud.cpu().numpy().reshape(3, -1), uh)
+    ref = oracle_run(Q, DIMS, flags, "CM", p, f0, 3)
+    assert rel_err(fh, ref.f, flags) <= RTOL_F64
+
+
+def test_state_errors():
+    flags = np.zeros(27, np.uint8)
+    with L.Lattice(19, 3, 3, 3, "aa", "BGK_W2", 1.0, flags) as g:
+        with pytest.raises(L.LBMError) as ei:
+            g.macroscopic()
+        assert ei.value.code == L.ERR_STATE
+        g.step(1)  # implicit rest equilibrium
+        with pytest.raises(L.LBMError) as ei:
+            L.lbm_set_precision(g.h, L.F32)
+        assert ei.value.code == L.ERR_STATE
+        with pytest.raises(L.LBMError) as ei:
+            g.step(-1)
+        assert ei.value.code == L.ERR_INVALID_ARG
+        m, _ = g.reduce()
+        assert abs(m - 27.0) < 1e-12
+    with L.Lattice(19, 3, 3, 3, "aa", "BGK_W2", 1.0, flags) as g:
+        with pytest.raises(L.LBMError) as ei:
+            L.lbm_set_layout(g.h, L.AOS) or L.lbm_set_precision(g.h, L.F32)
+        assert ei.value.code == L.ERR_UNSUPPORTED
