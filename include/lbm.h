@@ -177,6 +177,33 @@ LBM_API int lbm_supported(int lattice, int scheme, int collision, int layout, in
 /* Text of the calling thread's last error ("" if none). */
 LBM_API const char* lbm_last_error(void);
 
+/* FP64 conserved sums over caller-owned device buffers, without allocating.
+ * No counterpart in the paper: this exists for callers that cannot let the
+ * library call cudaMalloc -- an application that hands out every device
+ * buffer from its own pool, a real-time loop that cannot take the implicit
+ * synchronisation of cudaMalloc/cudaFree, or an environment with a fixed
+ * device-memory budget.  It computes what lbm_reduce computes, from
+ * canonical populations instead of a handle.
+ *   lattice: 19 or 27.  N: cells, 1 <= N <= 33,554,432 (larger N is rejected
+ *   with LBM_ERR_INVALID_ARG: the fixed scratch holds partial sums for 16,384
+ *   blocks of 2,048 cells).  f: device pointer, FP64 canonical populations
+ *   [Q][N].  flags: device pointer, one byte per cell, 0 = fluid, 1..7 =
+ *   solid (solid cells are skipped).  out: device pointer to 2 doubles,
+ *   receives {sum rho, sum rho |u|^2 / 2} over fluid cells.  stream: a
+ *   cudaStream_t or NULL.  Asynchronous: out is written when the stream
+ *   reaches the kernels.
+ * Scratch: a 256 KiB array in device global memory, fixed in the library
+ * image, which every GPU that loads the library keeps until the process
+ * exits.  Its address is looked up (cudaGetSymbolAddress) on the first call
+ * made on each device, with that device current; make that first call before
+ * any stream capture.  All calls share the array: calls whose kernels overlap
+ * on the GPU (different streams, or concurrent host threads) race and must
+ * be serialised by the caller.  No cudaMalloc, cudaFree or allocating
+ * routine is called.  Non-device pointers are rejected with
+ * LBM_ERR_INVALID_ARG before any kernel runs. */
+LBM_API int lbm_conserved_sums_static(int lattice, int N, const double* f, const uint8_t* flags, double* out,
+                                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

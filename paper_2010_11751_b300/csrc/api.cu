@@ -62,6 +62,8 @@ bool is_device_pointer(const void* p) {
 }
 }  // namespace
 
+int lbm::set_error(int code, const char* msg) { return fail(code, msg); }
+
 struct lbm_s {
   int Q = 19, nx = 0, ny = 0, nz = 0, N = 0;
   int scheme = LBM_TWOPOP, model = BGK_W2, layout = SOA, prec = F64;

@@ -25,4 +25,7 @@ cudaError_t launch_reduce(int Q, int P, int L, int LD, const KArgs& a, double* p
                           cudaStream_t s);
 cudaError_t launch_swap_stream(int Q, int P, int L, const KArgs& a, int threads, cudaStream_t s);
 
+// record the calling thread's last error text (read back by lbm_last_error) and return code
+int set_error(int code, const char* msg);
+
 }  // namespace lbm

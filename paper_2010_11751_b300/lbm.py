@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         "lbm_bytes_per_cell_update": [vp, ctypes.POINTER(d)],
         "lbm_destroy": [vp],
         "lbm_supported": [i, i, i, i, i],
+        "lbm_conserved_sums_static": [i, i, dp, u8p, dp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -179,6 +180,12 @@ def lbm_destroy(h):
 
 def lbm_supported(lattice, scheme, collision, layout, precision):
     return bool(lib().lbm_supported(lattice, scheme, collision, layout, precision))
+
+
+def lbm_conserved_sums_static(lattice, N, f, flags, out, stream=None):
+    """FP64 {sum rho, sum rho|u|^2/2} of canonical device populations into device out[2];
+    allocates nothing (fixed library scratch; see include/lbm.h)."""
+    return _check(lib().lbm_conserved_sums_static(lattice, N, ptr(f), ptr(flags), ptr(out), stream))
 
 
 def lbm_last_error():
