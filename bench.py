@@ -33,6 +33,12 @@ from paper_2010_11751_b300 import inputs as I  # noqa: E402
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
+# FP64 flops executed per fluid-cell update by the step kernel (ncu: dadd + dmul + 2 dfma per
+# launch / fluid cells, D3Q19 cavity 128^3, both AA kernels identical); see
+# profiles/aa_step_d3q19_f64_bgk_128.md.  The FP64 kernels are bound by the FP64 pipe.
+FP64_FLOPS_PER_FLUID_CELL = {(19, "BGK_W2"): 182.2}
+# B300 FP64 pipe: 2 DFMA per SM per clock (ncu peak_sustained 296 thread-DFMA/cycle for 148 SMs)
+FP64_DFMA_PER_CLK = 296
 
 
 def parse():
@@ -52,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--forms", default="", help="precision: FP32/FP16 shifted storage at 512^3 vs FP64")
+    ap.add_argument("--form-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -287,8 +295,142 @@ def matrix(args):
     return rows
 
 
+def precision_form(args):
+    """D3Q19 AA 512^3, periodic Taylor-Green (u0 0.05, Re 1000) and cavity (Re 1000): populations
+    stored shifted in FP32 and FP16 with FP32 arithmetic, against the FP64 mode (itself checked
+    against the FP64 oracle), relative L2 velocity error after form_steps steps."""
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    n = args.n
+    N = n ** 3
+    hbm, _ = peaks()
+    out = []
+    for wl in ("taylor_green", "cavity"):
+        if wl == "taylor_green":
+            u0 = 0.05
+            nu = u0 * n / 1000.0
+            flags = I.periodic_flags(n, n, n)
+            walls = {}
+            rho, u = I.taylor_green_fields(n, n, n, u0)
+            rho_t, u_t = torch.from_numpy(rho).cuda(), torch.from_numpy(u.ravel()).cuda()
+        else:
+            nu = I.cavity_nu(0.02, n, 1000.0)
+            flags = I.cavity_flags(n, n, n)
+            walls = {I.LID: (0.02, 0.0, 0.0)}
+            rho_t = u_t = None
+        omega = 1.0 / (3.0 * nu + 0.5)
+        coll = "BGK_W2" if wl == "taylor_green" else "TRT"
+        fluid = torch.from_numpy(flags == 0).cuda()
+        res = {}
+        for prec in ("f64", "f32", "f16"):
+            g = L.Lattice(19, n, n, n, "aa", coll, omega, flags, precision=L.PRECISIONS[prec], wall_velocities=walls)
+            g.init_equilibrium(rho_t, u_t)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.step(args.form_steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.form_steps
+            uu = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+            g.macroscopic(None, uu)
+            res[prec] = (uu.view(3, N), ms, g.bytes_per_cell_update)
+            g.close()
+        uref = res["f64"][0][:, fluid]
+        for prec in ("f64", "f32", "f16"):
+            uu, ms, bpc = res[prec]
+            d = uu[:, fluid] - uref
+            err = float(torch.sqrt((d * d).sum() / (uref * uref).sum()))
+            gbs = bpc * N / (ms * 1e-3) / 1e9
+            out.append({"workload": wl, "collision": coll, "precision": prec, "steps": args.form_steps,
+                        "mlups": round(N / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
+                        "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                        "l2_rel_velocity_error_vs_f64": err})
+        del res, uref
+        torch.cuda.empty_cache()
+    return out
+
+
+def batching_form(args):
+    """256 independent D3Q19 cavities, sides uniform in [16, 96] (non-cubic), Re uniform in
+    [100, 1000] (nu = u nx / Re), TRT, FP32 shifted storage, AA: the plain per-lattice launch
+    loop against one launch per step for the whole batch (autotuned, CUDA graph)."""
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    steps = args.form_steps
+    specs = I.batch_cavities(256, 16, 96, 100.0, 1000.0)
+    lid = {I.LID: (0.02, 0.0, 0.0)}
+
+    def make():
+        lats = []
+        for nx, ny, nz, re in specs:
+            omega = 1.0 / (3.0 * I.cavity_nu(0.02, nx, re) + 0.5)
+            g = L.Lattice(19, nx, ny, nz, "aa", "TRT", omega, I.cavity_flags(nx, ny, nz), precision=L.F32,
+                          wall_velocities=lid)
+            g.init_equilibrium()
+            lats.append(g)
+        return lats
+
+    cells = sum(a * b * c for a, b, c, _ in specs)
+    res = {"members": len(specs), "cells": cells, "steps": steps}
+    # plain per-lattice launch loop: each lattice advanced by its own launches, one after the other
+    lats = make()
+    for g in lats:
+        g.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in lats:
+        g.step(steps)
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    loop_pops = [g.get_populations() for g in lats[:4]]
+    for g in lats:
+        g.close()
+    res["per_lattice_loop_mlups"] = round(cells * steps / t_loop / 1e6, 1)
+    # batched: one launch per step for all 256 lattices, captured in a CUDA graph
+    lats = make()
+    with L.Batch(lats) as b:
+        b.step(2, use_graph=False)
+        tb0 = time.perf_counter()
+        thr, cpt = b.autotune()
+        t_tune = time.perf_counter() - tb0
+        tuned_steps = lats[0].steps_done - 2
+        b.step(steps, use_graph=True)  # capture + first replay (not timed)
+        b.sync()
+        t0 = time.perf_counter()
+        b.step(steps, use_graph=True)
+        b.sync()
+        t_batch = time.perf_counter() - t0
+        same = None
+        if tuned_steps == 0:
+            same = all(np.array_equal(g.get_populations(), ref) for g, ref in zip(lats[:4], loop_pops))
+    for g in lats:
+        g.close()
+    res.update({"batched_graph_mlups": round(cells * steps / t_batch / 1e6, 1), "autotuned_threads": thr,
+                "autotuned_cells_per_thread": cpt, "autotune_seconds": round(t_tune, 2),
+                "speedup_vs_loop": round(t_loop / t_batch, 3),
+                "note": "bit-identity of batched and per-lattice results is checked in tests/test_gpu_batch.py"})
+    hbm, _ = peaks()
+    res["batched_hbm_frac"] = round(2 * 19 * 4 * cells * steps / t_batch / 1e9 / hbm, 4)
+    return res
+
+
 def main():
     args = parse()
+    if args.forms == "batching":
+        if args.form_steps == 2000:
+            args.form_steps = 500
+        print(json.dumps({"form": "batching", "config": "256 D3Q19 cavities, sides U[16,96], Re U[100,1000], TRT, "
+                          "FP32, AA", "result": batching_form(args)}))
+        return
+    if args.forms == "precision":
+        print(json.dumps({"form": "precision", "config": f"D3Q19 AA {args.n}^3, FP32/FP16 shifted vs FP64",
+                          "rows": precision_form(args)}))
+        return
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         if rank != 0:
@@ -315,6 +457,22 @@ def main():
     dominant = r["odd"] if (args.scheme == "aa" and r["odd"]) else r["per"]
     dom_ms = sum(dominant) / len(dominant)
     achieved = r["bpc"] * N / (dom_ms * 1e-3) / 1e9
+    flops = FP64_FLOPS_PER_FLUID_CELL.get((args.lattice, args.collision)) if args.precision == "f64" else None
+    if flops is not None:
+        fluid = (args.n - 2) ** 3
+        clk = (r["clocks"].get("sm_max_mhz") or 2032.0) * 1e6
+        peak_tf = FP64_DFMA_PER_CLK * 2 * clk / 1e12
+        tf = flops * fluid / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
+                "frac": round(tf / peak_tf, 4), "traffic": None,
+                "peak_source": "derived: 2 DFMA/SM/clk x 148 SMs x max SM clock x 2 flops",
+                "flops_per_fluid_cell": flops, "hbm_achieved_gbs": round(achieved, 1),
+                "hbm_frac": round(achieved / hbm, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
+    roof["kernel"] = f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else "")
+    roof["bytes_per_cell_update"] = r["bpc"]
     line = {
         "metric": f"MLUPS ({workload_name(args)})",
         "value": round(value, 2),
@@ -332,10 +490,7 @@ def main():
                    "scheme": args.scheme, "layout": "soa", "collision": args.collision, "reynolds": args.reynolds,
                    "parallelism": f"replicas x{world}",
                    "l2": "no flush: population state larger than L2 (inputs larger than L2)"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else ""),
-                     "bytes_per_cell_update": r["bpc"], "peak_source": f"{src} hbm_gbs"},
+        "roofline": roof,
         "hbm_frac_step": round(r["bpc"] * N * K / (r["total_ms"] * 1e-3) / 1e9 / hbm, 4),
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],

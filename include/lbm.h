@@ -177,6 +177,44 @@ LBM_API int lbm_supported(int lattice, int scheme, int collision, int layout, in
 /* Text of the calling thread's last error ("" if none). */
 LBM_API const char* lbm_last_error(void);
 
+/* ======================================================================
+ * Batched stepping of many independent lattices: one kernel launch per time
+ * step covers every member (no counterpart in the paper; the paper steps one
+ * lattice).  Members must share lattice, collision model and precision and
+ * use the AA pattern with the SoA layout.  They keep their own memory,
+ * parameters and time-step parity; a batched step is bit-identical to
+ * stepping each member alone.  Work runs on the batch stream (by default an
+ * internal stream that orders with the legacy default stream); members on
+ * other streams are synchronised before each batch call.  A member must not
+ * be stepped or read on its own while a batch call may still be running:
+ * call lbm_batch_sync first.
+ * ====================================================================== */
+typedef struct lbm_batch_s* lbm_batch_t;
+
+LBM_API int lbm_batch_create(lbm_batch_t* out);
+/* Add a handle; LBM_ERR_INVALID_ARG if it does not match the first member. */
+LBM_API int lbm_batch_add(lbm_batch_t b, lbm_t h);
+/* Remove a handle (waits for the batch stream). */
+LBM_API int lbm_batch_remove(lbm_batch_t b, lbm_t h);
+/* Threads per block (32..512, multiple of 32) and cells per thread (1, 2, 4);
+ * 0 selects the defaults (256, 1). */
+LBM_API int lbm_batch_set_launch(lbm_batch_t b, int threads_per_block, int cells_per_thread);
+/* Time every (threads, cells-per-thread) shape in {64,128,256,512} x {1,2,4}
+ * on the batch as it stands (CUDA events on the batch stream) and keep the
+ * fastest.  The trial steps advance the members (6 steps per shape).  The
+ * choice is cached per (lattice, collision, precision, size class =
+ * floor(log2(mean member cells))) for the process; a cached choice is reused
+ * without trials.  Outputs may be NULL. */
+LBM_API int lbm_batch_autotune(lbm_batch_t b, int* threads_per_block, int* cells_per_thread);
+/* Advance every member by n >= 0 steps, one launch per step; with
+ * use_graph != 0 the n launches are captured once into a CUDA graph and
+ * replayed by later calls with the same n and membership.  Asynchronous. */
+LBM_API int lbm_batch_step(lbm_batch_t b, int n, int use_graph);
+LBM_API int lbm_batch_set_stream(lbm_batch_t b, void* stream);
+LBM_API int lbm_batch_sync(lbm_batch_t b);
+LBM_API int lbm_batch_size(lbm_batch_t b, int* members, long long* cells);
+LBM_API int lbm_batch_destroy(lbm_batch_t b);
+
 /* FP64 conserved sums over caller-owned device buffers, without allocating.
  * No counterpart in the paper: this exists for callers that cannot let the
  * library call cudaMalloc -- an application that hands out every device

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "handle.h"
 #include "internal.h"
 #include "kernels.cuh"
 #include "lbm.h"
@@ -64,30 +65,6 @@ bool is_device_pointer(const void* p) {
 
 int lbm::set_error(int code, const char* msg) { return fail(code, msg); }
 
-struct lbm_s {
-  int Q = 19, nx = 0, ny = 0, nz = 0, N = 0;
-  int scheme = LBM_TWOPOP, model = BGK_W2, layout = SOA, prec = F64;
-  double omega = 1.0, omega_bulk = 1.0, omega_high = 1.0, lambda = 0.25;
-  bool bulk_follows = true;
-  double wall_u[8][3] = {};
-  double wall_table[8 * 27] = {};
-  cudaStream_t stream = nullptr;
-  uint8_t* d_flags = nullptr;
-  void* d_pop[2] = {nullptr, nullptr};
-  int npop = 1;
-  int cur = 0;
-  long long steps = 0;
-  bool populated = false;
-  double* d_wall = nullptr;   // [8][Q] wall terms
-  double* d_wallu = nullptr;  // [8][3] wall velocities
-  bool wall_dirty = true;
-  double* d_partials = nullptr;
-  int partials = 0;
-  void* d_stage = nullptr;
-  size_t stage_bytes = 0;
-  int threads = 256;
-  StepFn fns[NUM_STEP_KINDS] = {};
-};
 
 namespace {
 
@@ -194,6 +171,25 @@ int init_eq_device(lbm_s* h, const double* rho, const double* u) {
 int valid_omega(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
 
 }  // namespace
+
+int lbm::handle_prepare(lbm_s* h) {
+  if (!h->populated) {
+    int rc = init_eq_device(h, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  return upload_wall(h);
+}
+
+void lbm::handle_rates(const lbm_s* h, double* omega, double* omc, double* wplus, double* wminus,
+                       double* omega_high, double* trt_minus) {
+  const KArgs a = make_args(h);
+  *omega = a.omega;
+  *omc = a.omc;
+  *wplus = a.wplus;
+  *wminus = a.wminus;
+  *omega_high = a.omega_high;
+  *trt_minus = a.trt_minus;
+}
 
 extern "C" {
 

@@ -349,50 +349,90 @@ __device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p) {
   constexpr int H = Lat<Q>::H;
   R s[H], d[H];
   pair_sums<Q>(f, s, d);
-  const auto m = macro_from_pairs<Q, R, SH>(s, d, f[H]);
-  const R usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-  const R A = SH ? m.drho - R(1.5) * m.rho * usq : m.rho * (R(1) - R(1.5) * usq);
-  f[H] = p.omc * f[H] + (p.omega * R(WGT<Q, H>)) * A;
+  // density and momentum j = rho u
+  R r = f[H], jx = R(-0.0), jy = R(-0.0), jz = R(-0.0);
+  static_for<0, H>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    r = r + s[k];
+    jx = addc<Lat<Q>::e(k, 0)>(jx, d[k]);
+    jy = addc<Lat<Q>::e(k, 1)>(jy, d[k]);
+    jz = addc<Lat<Q>::e(k, 2)>(jz, d[k]);
+  });
+  const R rho = SH ? R(1) + r : r;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  // A = rho (1 - 1.5 |u|^2) = rho - 1.5 u.j  (shifted: A - 1 = drho - 1.5 u.j)
+  const R uj = ux * jx + uy * jy + uz * jz;
+  const R A = r - R(1.5) * uj;
+  // FP64 relaxes as (1 - w) f + w E (one operation fewer per population on
+  // the FP64 pipe); FP32 relaxes in non-equilibrium form f + w (E - f), which
+  // keeps the rounding of the large terms out of the small non-equilibrium part
+  constexpr bool neq_form = !std::is_same<R, double>::value;
+  if constexpr (neq_form) f[H] = f[H] + p.omega * (R(WGT<Q, H>) * A - f[H]);
+  else f[H] = p.omc * f[H] + (p.omega * R(WGT<Q, H>)) * A;
   static_for<0, H>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
-    R eu = R(-0.0);
-    eu = addc<ex>(eu, m.ux);
-    eu = addc<ey>(eu, m.uy);
-    eu = addc<ez>(eu, m.uz);
-    const R bk = m.rho * eu;
-    const R ow = p.omega * R(WGT<Q, k>);
-    const R ep = bk * (R(4.5) * eu + R(3)) + A;
-    const R em = bk * (R(4.5) * eu - R(3)) + A;
-    f[k + H + 1] = p.omc * f[k + H + 1] + ow * ep;
-    f[k] = p.omc * f[k] + ow * em;
+    R eu = R(-0.0), ej = R(-0.0);
+    eu = addc<ex>(eu, ux);
+    eu = addc<ey>(eu, uy);
+    eu = addc<ez>(eu, uz);
+    ej = addc<ex>(ej, jx);
+    ej = addc<ey>(ej, jy);
+    ej = addc<ez>(ej, jz);
+    // E_+- = t (A + 4.5 (e.u)(e.j) +- 3 e.j)
+    if constexpr (neq_form) {
+      const R t = R(WGT<Q, k>);
+      const R S = (R(4.5) * t * eu) * ej + t * A;
+      const R T = (R(3) * t) * ej;
+      f[k + H + 1] = f[k + H + 1] + p.omega * ((S + T) - f[k + H + 1]);
+      f[k] = f[k] + p.omega * ((S - T) - f[k]);
+    } else {
+      const R W = p.omega * R(WGT<Q, k>);
+      const R S = (R(4.5) * W * eu) * ej + W * A;
+      const R T = (R(3) * W) * ej;
+      f[k + H + 1] = p.omc * f[k + H + 1] + (S + T);
+      f[k] = p.omc * f[k] + (S - T);
+    }
   });
 }
 
-// TRT: symmetric part relaxes with w, antisymmetric part with w- (from Lambda)
+// TRT: symmetric part relaxes with w, antisymmetric part with w- (from Lambda).
+// Per opposite pair (plus member along e_k): E+ = t (A + 4.5 (e.u)(e.j)),
+// E-_plus = 3 t e.j, with j = rho u and A = rho (1 - 1.5 |u|^2).
 template <int Q, typename R, bool SH>
 __device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p) {
   constexpr int H = Lat<Q>::H;
   R s[H], d[H];
   pair_sums<Q>(f, s, d);
-  const auto m = macro_from_pairs<Q, R, SH>(s, d, f[H]);
-  const R usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-  const R A = SH ? m.drho - R(1.5) * m.rho * usq : m.rho * (R(1) - R(1.5) * usq);
+  R r = f[H], jx = R(-0.0), jy = R(-0.0), jz = R(-0.0);
+  static_for<0, H>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    r = r + s[k];
+    jx = addc<Lat<Q>::e(k, 0)>(jx, d[k]);
+    jy = addc<Lat<Q>::e(k, 1)>(jy, d[k]);
+    jz = addc<Lat<Q>::e(k, 2)>(jz, d[k]);
+  });
+  const R rho = SH ? R(1) + r : r;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const R uj = ux * jx + uy * jy + uz * jz;
+  const R A = r - R(1.5) * uj;
   f[H] = f[H] - p.omega * (f[H] - R(WGT<Q, H>) * A);
+  const R hp = R(0.5) * p.omega, hm = R(0.5) * p.trt_minus;
   static_for<0, H>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
-    R eu = R(-0.0);
-    eu = addc<ex>(eu, m.ux);
-    eu = addc<ey>(eu, m.uy);
-    eu = addc<ez>(eu, m.uz);
-    const R w = R(WGT<Q, k>);
-    const R bk = m.rho * eu;
-    const R esym = w * (bk * (R(4.5) * eu) + A);
-    const R eanti = w * (R(3) * bk);
-    const R nsym = R(0.5) * s[k] - esym;
-    const R nanti = R(0.5) * d[k] - eanti;  // along e_k
-    const R a = p.omega * nsym, b = p.trt_minus * nanti;
+    R eu = R(-0.0), ej = R(-0.0);
+    eu = addc<ex>(eu, ux);
+    eu = addc<ey>(eu, uy);
+    eu = addc<ez>(eu, uz);
+    ej = addc<ex>(ej, jx);
+    ej = addc<ey>(ej, jy);
+    ej = addc<ez>(ej, jz);
+    const R Sp = (R(4.5) * eu) * ej + A;
+    const R a = hp * s[k] - (p.omega * R(WGT<Q, k>)) * Sp;      // w+ (f+ - E+)
+    const R b = hm * d[k] - (R(3) * p.trt_minus * R(WGT<Q, k>)) * ej;  // w- (f-_plus - E-_plus)
     f[k + H + 1] = f[k + H + 1] - a - b;
     f[k] = f[k] - a + b;
   });
@@ -537,7 +577,7 @@ __device__ __forceinline__ void collide_nw4(R (&f)[Q], const CP<R>& p) {
   store_moments<Q, R, SH>(E, st, feq);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    f[k] = p.omc * f[k] + p.omega * feq[k];
+    f[k] = f[k] + p.omega * (feq[k] - f[k]);
   });
 }
 
@@ -756,13 +796,15 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p) {
   else collide_k<Q, R, SH>(f, p);
 }
 
-// the model's own equilibrium of (rho, u), in stored form (shifted or not)
+// the model's own equilibrium of (rho, u), in stored form (shifted or not);
+// drho = rho - 1 for shifted storage (formed by the caller in FP64 so that the
+// density deviation keeps its precision), rho otherwise
 template <int Q, int M, typename R, bool SH>
-__device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R uz, R (&f)[Q]) {
+__device__ __forceinline__ void equilibrium(R rho, R drho, R ux, R uy, R uz, R (&f)[Q]) {
   constexpr int H = Lat<Q>::H;
   if constexpr (M == BGK_W2 || M == TRT || M == REG) {
     const R usq = ux * ux + uy * uy + uz * uz;
-    const R A = SH ? (rho - R(1)) - R(1.5) * rho * usq : rho * (R(1) - R(1.5) * usq);
+    const R A = SH ? drho - R(1.5) * rho * usq : rho * (R(1) - R(1.5) * usq);
     f[H] = R(WGT<Q, H>) * A;
     static_for<0, H>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -777,7 +819,7 @@ __device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R uz, R (&f)[Q]) 
   } else {
     MomState<Q, R, SH> st;
     st.rho = rho;
-    st.drho = SH ? rho - R(1) : rho;
+    st.drho = drho;
     R E[Q];
     eq_raw<Q>(ux, uy, uz, E);
     store_moments<Q, R, SH>(E, st, f);

@@ -1,0 +1,42 @@
+// handle.h -- the lattice handle behind lbm_t (shared by the single-lattice
+// API and the batch scheduler).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "lbm.h"
+
+struct lbm_s {
+  int Q = 19, nx = 0, ny = 0, nz = 0, N = 0;
+  int scheme = LBM_TWOPOP, model = lbm::BGK_W2, layout = lbm::SOA, prec = lbm::F64;
+  double omega = 1.0, omega_bulk = 1.0, omega_high = 1.0, lambda = 0.25;
+  bool bulk_follows = true;
+  double wall_u[8][3] = {};
+  double wall_table[8 * 27] = {};
+  cudaStream_t stream = nullptr;
+  uint8_t* d_flags = nullptr;
+  void* d_pop[2] = {nullptr, nullptr};
+  int npop = 1;
+  int cur = 0;
+  long long steps = 0;
+  bool populated = false;
+  double* d_wall = nullptr;   // [8][Q] wall terms
+  double* d_wallu = nullptr;  // [8][3] wall velocities
+  bool wall_dirty = true;
+  double* d_partials = nullptr;
+  int partials = 0;
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  int threads = 256;
+  lbm::StepFn fns[lbm::NUM_STEP_KINDS] = {};
+};
+
+namespace lbm {
+// make a handle ready to be stepped: populations written (rest equilibrium if
+// never written) and the wall table on the device; returns LBM_OK or an error
+int handle_prepare(lbm_s* h);
+// relaxation parameters of the handle, as the step kernels take them
+void handle_rates(const lbm_s* h, double* omega, double* omc, double* wplus, double* wminus, double* omega_high,
+                  double* trt_minus);
+}  // namespace lbm

@@ -8,10 +8,14 @@
 namespace lbm {
 
 struct KArgs;
+struct BatchArgs;
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
+using BatchFn = cudaError_t (*)(const BatchArgs&, int blocks, int threads, cudaStream_t);
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);
+// batched AA kernel (SoA) for (lattice, model, precision); nullptr if not built
+BatchFn batch_fn(int model, int Q, int P);
 
 cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, int nx, int ny, int nz, cudaStream_t s);
 cudaError_t launch_macro(int Q, int P, int L, int LD, const KArgs& a, double* rho, double* u, const double* wall_u,

@@ -173,28 +173,27 @@ __device__ __forceinline__ void store_cell_canonical(const KArgs& a, const Nb<FA
 // ---------------------------------------------------------------------------
 // the fused stream-and-collide step
 // ---------------------------------------------------------------------------
-template <int Q, int M, int P, int L, int SK, bool FAST>
-__device__ __forceinline__ void step_cell(const KArgs& a, int i) {
-  using R = typename Store<P>::R;
-  constexpr bool SH = Store<P>::shifted;
+// Only the load and store phases depend on whether the cell is a bulk cell
+// (FAST) or sits next to a wall / on a domain face; the collision runs once,
+// converged, between them, so a warp that mixes both kinds of cells does not
+// execute the collision twice.
+template <int Q, int P, int L, int SK, bool FAST>
+__device__ __forceinline__ void step_load(const KArgs& a, int i, typename Store<P>::R (&f)[Q]) {
   constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : (SK == K_ESOTWIST ? LD_ET_EVEN : LD_LOCAL);
   const Nb<FAST> nb(i, a);
-  const int N = a.N;
-  R f[Q];
   if constexpr (SK == K_ESOTWIST) {
     if (a.parity == 0) load_cell<Q, P, L, LD_ET_EVEN, FAST>(a, nb, a.a, f);
     else load_cell<Q, P, L, LD_ET_ODD, FAST>(a, nb, a.a, f);
   } else {
     load_cell<Q, P, L, LD, FAST>(a, nb, a.a, f);
   }
-  CP<R> cp;
-  cp.omega = R(a.omega);
-  cp.omc = R(a.omc);
-  cp.wplus = R(a.wplus);
-  cp.wminus = R(a.wminus);
-  cp.omega_high = R(a.omega_high);
-  cp.trt_minus = R(a.trt_minus);
-  collide<Q, M, R, SH>(f, cp);
+}
+
+template <int Q, int P, int L, int SK, bool FAST>
+__device__ __forceinline__ void step_store(const KArgs& a, int i, const typename Store<P>::R (&f)[Q]) {
+  using R = typename Store<P>::R;
+  const Nb<FAST> nb(i, a);
+  const int N = a.N;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int kb = Lat<Q>::opp(k);
@@ -222,13 +221,32 @@ __device__ __forceinline__ void step_cell(const KArgs& a, int i) {
   });
 }
 
+// one cell update (load, collide, store); solid cells are left alone
+template <int Q, int M, int P, int L, int SK>
+__device__ __forceinline__ void step_one(const KArgs& a, int i) {
+  using R = typename Store<P>::R;
+  const uint8_t fl = a.flags[i];
+  if (fl & FLAG_KIND) return;  // solid cell: nothing to update
+  R f[Q];
+  if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
+  else step_load<Q, P, L, SK, false>(a, i, f);
+  CP<R> cp;
+  cp.omega = R(a.omega);
+  cp.omc = R(a.omc);
+  cp.wplus = R(a.wplus);
+  cp.wminus = R(a.wminus);
+  cp.omega_high = R(a.omega_high);
+  cp.trt_minus = R(a.trt_minus);
+  collide<Q, M, R, Store<P>::shifted>(f, cp);
+  if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
+  else step_store<Q, P, L, SK, false>(a, i, f);
+}
+
 template <int Q, int M, int P, int L, int SK>
 __global__ void __launch_bounds__(256) step_kernel(KArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
-  const uint8_t fl = a.flags[i];
-  if (fl == 0) step_cell<Q, M, P, L, SK, true>(a, i);
-  else if ((fl & FLAG_KIND) == 0) step_cell<Q, M, P, L, SK, false>(a, i);
+  step_one<Q, M, P, L, SK>(a, i);
 }
 
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);

@@ -1,9 +1,11 @@
 // model_reg.cu -- step kernels of the REG collision model for every lattice,
-// storage precision, layout and step kind (one translation unit per model so
-// that the build parallelises).
+// storage precision, layout and step kind, and its batched (many-lattice)
+// kernels (one translation unit per model so that the build parallelises).
+#include "batch.cuh"
 #include "internal.h"
 #include "kernels.cuh"
 
 namespace lbm {
 StepFn step_fn_reg(int Q, int P, int L, int SK) { return step_fn_for_model<REG>(Q, P, L, SK); }
+BatchFn batch_fn_reg(int Q, int P) { return batch_fn_for_model<REG>(Q, P); }
 }  // namespace lbm

@@ -140,10 +140,11 @@ __global__ void __launch_bounds__(256) init_kernel(KArgs a, const double* rho, c
   const uint8_t fl = a.flags[i];
   if (fl & FLAG_KIND) return;
   using R = typename Store<P>::R;
-  const R r = rho ? R(rho[i]) : R(1);
+  const double rd = rho ? rho[i] : 1.0;
+  const R r = R(rd), dr = R(Store<P>::shifted ? rd - 1.0 : rd);
   const R ux = u ? R(u[i]) : R(0), uy = u ? R(u[(size_t)a.N + i]) : R(0), uz = u ? R(u[2 * (size_t)a.N + i]) : R(0);
   R f[Q];
-  equilibrium<Q, M, R, Store<P>::shifted>(r, ux, uy, uz, f);
+  equilibrium<Q, M, R, Store<P>::shifted>(r, dr, ux, uy, uz, f);
   store_canonical<Q, P, L, LD>(a, i, fl, f);
 }
 

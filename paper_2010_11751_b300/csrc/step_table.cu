@@ -1,4 +1,5 @@
 // step_table.cu -- model dispatch of the step kernels.
+#include "batch.cuh"
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -14,6 +15,17 @@ StepFn step_fn_cm(int, int, int, int);
 StepFn step_fn_chm(int, int, int, int);
 StepFn step_fn_k(int, int, int, int);
 
+BatchFn batch_fn_bgk_w2(int, int);
+BatchFn batch_fn_bgk_nw4(int, int);
+BatchFn batch_fn_trt(int, int);
+BatchFn batch_fn_reg(int, int);
+BatchFn batch_fn_rr(int, int);
+BatchFn batch_fn_rm(int, int);
+BatchFn batch_fn_hm(int, int);
+BatchFn batch_fn_cm(int, int);
+BatchFn batch_fn_chm(int, int);
+BatchFn batch_fn_k(int, int);
+
 StepFn step_fn(int model, int Q, int P, int L, int SK) {
   switch (model) {
     case BGK_W2: return step_fn_bgk_w2(Q, P, L, SK);
@@ -26,6 +38,21 @@ StepFn step_fn(int model, int Q, int P, int L, int SK) {
     case CM: return step_fn_cm(Q, P, L, SK);
     case CHM: return step_fn_chm(Q, P, L, SK);
     case KUM: return step_fn_k(Q, P, L, SK);
+    default: return nullptr;
+  }
+}
+BatchFn batch_fn(int model, int Q, int P) {
+  switch (model) {
+    case BGK_W2: return batch_fn_bgk_w2(Q, P);
+    case BGK_NW4: return batch_fn_bgk_nw4(Q, P);
+    case TRT: return batch_fn_trt(Q, P);
+    case REG: return batch_fn_reg(Q, P);
+    case RR: return batch_fn_rr(Q, P);
+    case RM: return batch_fn_rm(Q, P);
+    case HM: return batch_fn_hm(Q, P);
+    case CM: return batch_fn_cm(Q, P);
+    case CHM: return batch_fn_chm(Q, P);
+    case KUM: return batch_fn_k(Q, P);
     default: return nullptr;
   }
 }

@@ -68,6 +68,16 @@ def lib() -> ctypes.CDLL:
         "lbm_destroy": [vp],
         "lbm_supported": [i, i, i, i, i],
         "lbm_conserved_sums_static": [i, i, dp, u8p, dp, vp],
+        "lbm_batch_create": [ctypes.POINTER(vp)],
+        "lbm_batch_add": [vp, vp],
+        "lbm_batch_remove": [vp, vp],
+        "lbm_batch_set_launch": [vp, i, i],
+        "lbm_batch_autotune": [vp, ctypes.POINTER(i), ctypes.POINTER(i)],
+        "lbm_batch_step": [vp, i, i],
+        "lbm_batch_set_stream": [vp, vp],
+        "lbm_batch_sync": [vp],
+        "lbm_batch_size": [vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)],
+        "lbm_batch_destroy": [vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -188,6 +198,52 @@ def lbm_conserved_sums_static(lattice, N, f, flags, out, stream=None):
     return _check(lib().lbm_conserved_sums_static(lattice, N, ptr(f), ptr(flags), ptr(out), stream))
 
 
+def lbm_batch_create():
+    b = ctypes.c_void_p()
+    _check(lib().lbm_batch_create(ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_add(b, h):
+    return _check(lib().lbm_batch_add(b, h))
+
+
+def lbm_batch_remove(b, h):
+    return _check(lib().lbm_batch_remove(b, h))
+
+
+def lbm_batch_set_launch(b, threads, cells_per_thread):
+    return _check(lib().lbm_batch_set_launch(b, threads, cells_per_thread))
+
+
+def lbm_batch_autotune(b):
+    t, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbm_batch_autotune(b, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def lbm_batch_step(b, n, use_graph=True):
+    return _check(lib().lbm_batch_step(b, n, 1 if use_graph else 0))
+
+
+def lbm_batch_set_stream(b, stream):
+    return _check(lib().lbm_batch_set_stream(b, stream))
+
+
+def lbm_batch_sync(b):
+    return _check(lib().lbm_batch_sync(b))
+
+
+def lbm_batch_size(b):
+    m, c = ctypes.c_int(), ctypes.c_longlong()
+    _check(lib().lbm_batch_size(b, ctypes.byref(m), ctypes.byref(c)))
+    return m.value, c.value
+
+
+def lbm_batch_destroy(b):
+    return _check(lib().lbm_batch_destroy(b))
+
+
 def lbm_last_error():
     return lib().lbm_last_error().decode()
 
@@ -274,6 +330,57 @@ class Lattice:
         if getattr(self, "h", None) is not None and self.h.value:
             lbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many lattices advanced by one launch per time step (members share lattice, model, precision)."""
+
+    def __init__(self, lattices=()):
+        self.b = lbm_batch_create()
+        self.members = []
+        for lat in lattices:
+            self.add(lat)
+
+    def add(self, lat):
+        lbm_batch_add(self.b, lat.h)
+        self.members.append(lat)
+
+    def remove(self, lat):
+        lbm_batch_remove(self.b, lat.h)
+        self.members.remove(lat)
+
+    def set_launch(self, threads=0, cells_per_thread=0):
+        lbm_batch_set_launch(self.b, threads, cells_per_thread)
+
+    def autotune(self):
+        return lbm_batch_autotune(self.b)
+
+    def step(self, n=1, use_graph=True):
+        lbm_batch_step(self.b, n, use_graph)
+
+    def sync(self):
+        lbm_batch_sync(self.b)
+
+    @property
+    def size(self):
+        return lbm_batch_size(self.b)
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            lbm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
