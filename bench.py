@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--forms", default="", help="precision: FP32/FP16 shifted storage at 512^3 vs FP64")
     ap.add_argument("--form-steps", type=int, default=2000)
+    ap.add_argument("--trace", type=int, default=500, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrival rate (1/s)")
+    ap.add_argument("--tick", type=int, default=64, help="serving: steps per tick")
     return ap.parse_args()
 
 
@@ -419,8 +422,39 @@ def batching_form(args):
     return res
 
 
+def serving_form(args):
+    """Poisson trace (mean args.rate/s and 20 % of it) of D3Q19/D3Q27 cavity or Taylor-Green
+    solves, side U[32,192], 100-2000 steps, BGK-W2 or cumulant, FP32 or FP64 (Re 100): continuous
+    batching against a plain FIFO queue (one solve at a time) on the same trace."""
+    import torch
+
+    from paper_2010_11751_b300.serve import GpuBackend, Scheduler, summarize, trace_requests
+
+    out = []
+    for rate in (args.rate, 0.2 * args.rate):
+        trace = trace_requests(I.serving_trace(args.trace, rate), reynolds=100.0)
+        for mode, limit in (("continuous_batching", None), ("fifo_queue_one_at_a_time", 1)):
+            be = GpuBackend()
+            sched = Scheduler(be, tick_steps=args.tick, reserve_bytes=8 << 30, max_active=limit)
+            t0 = time.perf_counter()
+            res = sched.run(trace)
+            wall = time.perf_counter() - t0
+            be.close()
+            torch.cuda.empty_cache()
+            s = summarize(res, wall)
+            s.update({"mode": mode, "rate_hz": rate, "ticks": sched.ticks, "max_active": sched.max_active,
+                      "offered_cell_updates": sum(r.side ** 3 * r.steps for r in trace)})
+            out.append(s)
+    return out
+
+
 def main():
     args = parse()
+    if args.forms == "serving":
+        print(json.dumps({"form": "serving", "config": f"{args.trace} requests, Poisson {args.rate:g}/s and "
+                          f"{0.2 * args.rate:g}/s, side U[32,192], 100-2000 steps, D3Q19/D3Q27, cavity/TG, BGK/K, "
+                          "FP32/FP64, Re 100", "rows": serving_form(args)}))
+        return
     if args.forms == "batching":
         if args.form_steps == 2000:
             args.form_steps = 500

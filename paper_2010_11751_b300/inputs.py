@@ -68,6 +68,21 @@ def taylor_green_fields(nx: int, ny: int, nz: int, u0: float, kx: float | None =
     return rho.ravel().astype(np.float64), u.astype(np.float64)
 
 
+def taylor_green_fields_torch(nx: int, ny: int, nz: int, u0: float, device: str = "cuda"):
+    """The same analytic Taylor-Green field as taylor_green_fields, built with torch on a device
+    (contiguous float64 rho[N] and u[3*N])."""
+    import torch
+
+    kx, ky = 2.0 * np.pi / nx, 2.0 * np.pi / ny
+    x = torch.arange(nx, dtype=torch.float64, device=device).view(nx, 1, 1).expand(nx, ny, nz)
+    y = torch.arange(ny, dtype=torch.float64, device=device).view(1, ny, 1).expand(nx, ny, nz)
+    ux = u0 * torch.cos(kx * x) * torch.sin(ky * y)
+    uy = -u0 * torch.sin(kx * x) * torch.cos(ky * y)
+    rho = 1.0 - 0.75 * u0 * u0 * (torch.cos(2 * kx * x) + torch.cos(2 * ky * y))
+    u = torch.stack([ux.reshape(-1), uy.reshape(-1), torch.zeros(nx * ny * nz, dtype=torch.float64, device=device)])
+    return rho.reshape(-1).contiguous(), u.reshape(-1).contiguous()
+
+
 def taylor_green_mode(nx: int, ny: int, nz: int, kx: float | None = None, ky: float | None = None) -> np.ndarray:
     """The spatial shape cos(kx x) sin(ky y) of the x-velocity, for amplitude fits."""
     kx = 2.0 * np.pi / nx if kx is None else kx
