@@ -229,6 +229,7 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
   h->model = collision;
   h->omega = omega;
   h->npop = scheme == LBM_TWOPOP ? 2 : 1;
+  h->threads = step_threads(h->prec);
   int rc = resolve_kernels(h);
   if (rc) {
     delete h;
@@ -282,6 +283,7 @@ int lbm_set_precision(lbm_t h, int precision) {
       h->d_pop[a] = nullptr;
     }
   h->prec = precision;
+  h->threads = step_threads(h->prec);
   return resolve_kernels(h);
 }
 

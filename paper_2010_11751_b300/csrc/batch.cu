@@ -235,7 +235,7 @@ int lbm_batch_set_launch(lbm_batch_t b, int threads, int cpt) {
   if (!b) return bfail(LBM_ERR_INVALID_ARG, "batch is NULL");
   if (threads == 0) threads = 256;
   if (cpt == 0) cpt = 1;
-  if (threads < 32 || threads > 512 || threads % 32) return bfail(LBM_ERR_INVALID_ARG, "threads must be 32..512, multiple of 32");
+  if (threads < 32 || threads > 256 || threads % 32) return bfail(LBM_ERR_INVALID_ARG, "threads must be 32..256, multiple of 32");
   if (cpt != 1 && cpt != 2 && cpt != 4) return bfail(LBM_ERR_INVALID_ARG, "cells per thread must be 1, 2 or 4");
   if (threads != b->threads || cpt != b->cpt) {
     b->threads = threads;
@@ -264,10 +264,10 @@ int lbm_batch_autotune(lbm_batch_t b, int* threads_out, int* cpt_out) {
   BCUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int bt = 256, bc = 1;
-  const int shapes_t[4] = {64, 128, 256, 512};
+  const int shapes_t[3] = {64, 128, 256};
   const int shapes_c[3] = {1, 2, 4};
   int rc = LBM_OK;
-  for (int ti = 0; ti < 4 && rc == LBM_OK; ++ti)
+  for (int ti = 0; ti < 3 && rc == LBM_OK; ++ti)
     for (int ci = 0; ci < 3 && rc == LBM_OK; ++ci) {
       rc = lbm_batch_set_launch(b, shapes_t[ti], shapes_c[ci]);
       if (rc) break;

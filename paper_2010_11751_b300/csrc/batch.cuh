@@ -30,8 +30,14 @@ struct BatchArgs {
   int cpt;                  // cells per thread
 };
 
+// the batch kernel holds both AA bodies and the cells-per-thread loop; register
+// caps that suit the single-lattice kernels make it spill, so it keeps the
+// default register budget
 template <int Q, int M, int P>
-__global__ void __launch_bounds__(512) batch_aa_kernel(BatchArgs b) {
+inline constexpr int BATCH_MIN_BLOCKS = 1;
+
+template <int Q, int M, int P>
+__global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kernel(BatchArgs b) {
   const int mi = __ldg(b.block_member + blockIdx.x);
   const Member* mm = b.m + mi;
   KArgs a;

@@ -221,15 +221,41 @@ __device__ __forceinline__ void step_store(const KArgs& a, int i, const typename
   });
 }
 
-// one cell update (load, collide, store); solid cells are left alone
+// one cell update (load, collide, store); solid cells are left alone.
+// The bulk-path loads (constant neighbour offsets) are issued before the cell's
+// flag byte has arrived, so that a bulk cell pays one memory round trip
+// instead of two.  They are issued only when every constant-offset address is
+// inside the array: a bulk cell (flag byte 0) is interior, hence its index lies
+// in [ny*nz + nz + 1, N - ny*nz - nz - 1), and the speculative loads of the
+// other cells in that range read valid memory and are discarded or redone
+// with exact addressing once the flag is known.
+// Measured on B300: the early loads pay off for the kernels that read only
+// their own cell (two-population, AA even / swap collision) in FP32 and FP64;
+// the neighbour-pulling kernels (AA odd, esoteric twist) and FP16 storage run
+// faster with the flag read first (fewer live registers).
+template <int P, int SK>
+__host__ __device__ constexpr bool early_loads() {
+  return P != F16 && SK != K_AA_ODD && SK != K_ESOTWIST;
+}
+
 template <int Q, int M, int P, int L, int SK>
 __device__ __forceinline__ void step_one(const KArgs& a, int i) {
   using R = typename Store<P>::R;
-  const uint8_t fl = a.flags[i];
-  if (fl & FLAG_KIND) return;  // solid cell: nothing to update
   R f[Q];
-  if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
-  else step_load<Q, P, L, SK, false>(a, i, f);
+  uint8_t fl;
+  if constexpr (early_loads<P, SK>()) {
+    const int reach = a.ny * a.nz + a.nz + 1;
+    const bool in_range = i >= reach && i < a.N - reach;
+    if (in_range) step_load<Q, P, L, SK, true>(a, i, f);
+    fl = a.flags[i];
+    if (fl & FLAG_KIND) return;  // solid cell: nothing to update
+    if (fl != 0) step_load<Q, P, L, SK, false>(a, i, f);
+  } else {
+    fl = a.flags[i];
+    if (fl & FLAG_KIND) return;
+    if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
+    else step_load<Q, P, L, SK, false>(a, i, f);
+  }
   CP<R> cp;
   cp.omega = R(a.omega);
   cp.omc = R(a.omc);
@@ -242,8 +268,18 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i) {
   else step_store<Q, P, L, SK, false>(a, i, f);
 }
 
+// FP32/FP16 kernels of the light models are bound by memory latency: capping
+// registers so that six (D3Q19) or four (D3Q27) 256-thread blocks fit per SM
+// measured fastest.  The moment models would spill under such caps, and FP64
+// kernels are bound by the FP64 pipe: both keep the default register budget.
+template <int Q, int M, int P>
+inline constexpr int MIN_BLOCKS =
+    (P == F64 || !(M == BGK_W2 || M == TRT || M == REG)) ? 1 : (Q == 19 ? 6 : 4);
+// threads per block of the single-lattice step kernels
+inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }
+
 template <int Q, int M, int P, int L, int SK>
-__global__ void __launch_bounds__(256) step_kernel(KArgs a) {
+__global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_kernel(KArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   step_one<Q, M, P, L, SK>(a, i);

@@ -94,7 +94,7 @@ def test_autotune_keeps_results():
             lst.append(g)
     with L.Batch(lats_a) as ba, L.Batch(lats_b) as bb:
         t, c = ba.autotune()
-        assert t in (64, 128, 256, 512) and c in (1, 2, 4)
+        assert t in (64, 128, 256) and c in (1, 2, 4)
         steps = lats_a[0].steps_done
         bb.step(steps, use_graph=False)
         ba.step(5)
