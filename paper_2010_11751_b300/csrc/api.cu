@@ -121,6 +121,7 @@ KArgs make_args(const lbm_s* h) {
   a.a = h->d_pop[h->cur];
   a.b = h->npop > 1 ? h->d_pop[1 - h->cur] : nullptr;
   a.flags = h->d_flags;
+  a.nbmask = h->d_nbmask;
   a.wall = h->d_wall;
   a.nx = h->nx;
   a.ny = h->ny;
@@ -237,9 +238,10 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
   }
   uint8_t* raw = nullptr;
   cudaError_t e = cudaMalloc(&h->d_flags, N);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_nbmask, sizeof(uint32_t) * N);
   if (e == cudaSuccess) e = cudaMalloc(&raw, N);
   if (e == cudaSuccess) e = cudaMemcpy(raw, flags, N, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = launch_classify(lattice, raw, h->d_flags, nx, ny, nz, h->stream);
+  if (e == cudaSuccess) e = launch_classify(lattice, raw, h->d_flags, h->d_nbmask, nx, ny, nz, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (raw) cudaFree(raw);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_wall, sizeof(double) * 8 * 27);
@@ -470,7 +472,8 @@ int lbm_steps_done(lbm_t h, long long* steps) {
 
 int lbm_device_bytes(lbm_t h, size_t* bytes) {
   if (!h || !bytes) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
-  size_t b = (size_t)h->N + sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2) + h->stage_bytes;
+  size_t b = (size_t)h->N * (1 + sizeof(uint32_t)) + sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2) +
+             h->stage_bytes;
   for (int a = 0; a < 2; ++a)
     if (h->d_pop[a]) b += pop_bytes(h);
   *bytes = b;
@@ -493,6 +496,7 @@ int lbm_destroy(lbm_t h) {
   for (int a = 0; a < 2; ++a)
     if (h->d_pop[a]) cudaFree(h->d_pop[a]);
   if (h->d_flags) cudaFree(h->d_flags);
+  if (h->d_nbmask) cudaFree(h->d_nbmask);
   if (h->d_wall) cudaFree(h->d_wall);
   if (h->d_wallu) cudaFree(h->d_wallu);
   if (h->d_partials) cudaFree(h->d_partials);

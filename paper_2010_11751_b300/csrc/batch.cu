@@ -105,6 +105,7 @@ int upload_members(lbm_batch_s* b) {
     Member& d = b->h_members[m];
     d.pop = h->d_pop[0];
     d.flags = h->d_flags;
+    d.nbmask = h->d_nbmask;
     d.wall = h->d_wall;
     d.nx = h->nx;
     d.ny = h->ny;

@@ -15,6 +15,7 @@ namespace lbm {
 struct __align__(16) Member {
   void* pop;
   const uint8_t* flags;
+  const uint32_t* nbmask;
   const double* wall;
   int nx, ny, nz, N;
   int parity0;      // parity of the member's step count when the batch call starts
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   a.a = mm->pop;
   a.b = nullptr;
   a.flags = mm->flags;
+  a.nbmask = mm->nbmask;
   a.wall = mm->wall;
   a.nx = mm->nx;
   a.ny = mm->ny;

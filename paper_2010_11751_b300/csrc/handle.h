@@ -16,6 +16,7 @@ struct lbm_s {
   double wall_table[8 * 27] = {};
   cudaStream_t stream = nullptr;
   uint8_t* d_flags = nullptr;
+  uint32_t* d_nbmask = nullptr;  // solid-neighbour bit mask per cell
   void* d_pop[2] = {nullptr, nullptr};
   int npop = 1;
   int cur = 0;

@@ -17,7 +17,8 @@ StepFn step_fn(int model, int Q, int P, int L, int SK);
 // batched AA kernel (SoA) for (lattice, model, precision); nullptr if not built
 BatchFn batch_fn(int model, int Q, int P);
 
-cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, uint32_t* mask, int nx, int ny, int nz,
+                            cudaStream_t s);
 cudaError_t launch_macro(int Q, int P, int L, int LD, const KArgs& a, double* rho, double* u, const double* wall_u,
                          cudaStream_t s);
 cudaError_t launch_get(int Q, int P, int L, int LD, const KArgs& a, double* out, cudaStream_t s);

@@ -40,6 +40,7 @@ struct KArgs {
   void* a;                // populations (current state)
   void* b;                // destination array of the two-population scheme
   const uint8_t* flags;   // classified flag bytes
+  const uint32_t* nbmask; // per fluid cell: bit k set when the neighbour along c_k is solid
   const double* wall;     // wall term table [8][Q]: -6 t_k c_k.u_w(kind)
   int nx, ny, nz, N;
   int parity;             // time-step parity (esoteric twist slot labels)
@@ -71,22 +72,34 @@ __device__ __forceinline__ void stp(void* base, size_t a, typename Store<P>::R v
 }
 
 // ---------------------------------------------------------------------------
-// neighbour access: FAST = interior bulk cell (no wrap, no solid neighbour)
+// neighbour access: FAST = interior bulk cell (no wrap, no solid neighbour).
+// Otherwise the cell's solid-neighbour mask tells which links bounce (a
+// neighbour's flag byte is read only for those, to find its wall kind), and
+// coordinates with periodic wrap are computed only for cells on a domain face.
 // ---------------------------------------------------------------------------
 template <bool FAST>
 struct Nb {
   int i, x, y, z;
   int nx, ny, nz, sxy;
+  bool edge;
+  uint32_t mask;
   const uint8_t* flags;
-  __device__ __forceinline__ Nb(int i_, const KArgs& a) : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
+  __device__ __forceinline__ Nb(int i_, const KArgs& a, uint8_t fl = 0)
+      : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
     sxy = a.ny * a.nz;
-    if constexpr (!FAST) {
-      x = i / sxy;
-      const int r = i - x * sxy;
-      y = r / nz;
-      z = r - y * nz;
+    x = y = z = 0;
+    if constexpr (FAST) {
+      edge = false;
+      mask = 0u;
     } else {
-      x = y = z = 0;
+      edge = (fl & FLAG_EDGE) != 0;
+      mask = (fl & FLAG_NEARWALL) ? __ldg(a.nbmask + i) : 0u;
+      if (edge) {
+        x = i / sxy;
+        const int r = i - x * sxy;
+        y = r / nz;
+        z = r - y * nz;
+      }
     }
   }
   // index of the cell at offset (dx, dy, dz), periodic
@@ -95,6 +108,7 @@ struct Nb {
     if constexpr (FAST) {
       return i + DX * sxy + DY * nz + DZ;
     } else {
+      if (!edge) return i + DX * sxy + DY * nz + DZ;
       int xn = x + DX, yn = y + DY, zn = z + DZ;
       if constexpr (DX != 0) xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
       if constexpr (DY != 0) yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
@@ -102,11 +116,16 @@ struct Nb {
       return (xn * ny + yn) * nz + zn;
     }
   }
-  // wall kind of the neighbour along c_k (0 = fluid)
+  // is the neighbour along c_k solid? (from the mask alone: no memory access)
+  template <int Q, int K>
+  __device__ __forceinline__ bool solid() const {
+    if constexpr (FAST) return false;
+    else return ((mask >> K) & 1u) != 0;
+  }
+  // wall kind of a solid neighbour along c_k (reads its flag byte)
   template <int Q, int K>
   __device__ __forceinline__ int kind() const {
-    if constexpr (FAST) return 0;
-    else return flags[at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>()] & FLAG_KIND;
+    return flags[at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>()] & FLAG_KIND;
   }
   template <int Q, int K>
   __device__ __forceinline__ int idx() const {
@@ -139,12 +158,12 @@ __device__ __forceinline__ void load_cell(const KArgs& a, const Nb<FAST>& nb, co
       ad = paddr<Q, L>(k, nb.i, N);
     } else if constexpr (LD == LD_AA_ODD) {
       // f_k(x) = pop_kbar(x - c_k) if x - c_k fluid, else pop_k(x)
-      if (nb.template kind<Q, kb>() == 0) ad = paddr<Q, L>(kb, nb.template idx<Q, kb>(), N);
+      if (!nb.template solid<Q, kb>()) ad = paddr<Q, L>(kb, nb.template idx<Q, kb>(), N);
       else ad = paddr<Q, L>(k, nb.i, N);
     } else {
       constexpr int PAR = LD == LD_ET_EVEN ? 0 : 1;
       const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
-      if (nb.template kind<Q, kb>() == 0) ad = paddr<Q, L>(et_slot<Q, k, PAR>(false), cell, N);
+      if (!nb.template solid<Q, kb>()) ad = paddr<Q, L>(et_slot<Q, k, PAR>(false), cell, N);
       else ad = paddr<Q, L>(et_slot<Q, k, PAR>(true), cell, N);
     }
     f[k] = T(ldp<P>(pop, ad));
@@ -164,7 +183,7 @@ __device__ __forceinline__ void store_cell_canonical(const KArgs& a, const Nb<FA
       ad = paddr<Q, L>(k, nb.i, N);
     } else {
       const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
-      ad = paddr<Q, L>(et_slot<Q, k, 0>(nb.template kind<Q, kb>() != 0), cell, N);
+      ad = paddr<Q, L>(et_slot<Q, k, 0>(nb.template solid<Q, kb>()), cell, N);
     }
     stp<P>(pop, ad, f[k]);
   });
@@ -178,9 +197,9 @@ __device__ __forceinline__ void store_cell_canonical(const KArgs& a, const Nb<FA
 // converged, between them, so a warp that mixes both kinds of cells does not
 // execute the collision twice.
 template <int Q, int P, int L, int SK, bool FAST>
-__device__ __forceinline__ void step_load(const KArgs& a, int i, typename Store<P>::R (&f)[Q]) {
+__device__ __forceinline__ void step_load(const KArgs& a, int i, typename Store<P>::R (&f)[Q], uint8_t fl = 0) {
   constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : (SK == K_ESOTWIST ? LD_ET_EVEN : LD_LOCAL);
-  const Nb<FAST> nb(i, a);
+  const Nb<FAST> nb(i, a, fl);
   if constexpr (SK == K_ESOTWIST) {
     if (a.parity == 0) load_cell<Q, P, L, LD_ET_EVEN, FAST>(a, nb, a.a, f);
     else load_cell<Q, P, L, LD_ET_ODD, FAST>(a, nb, a.a, f);
@@ -190,9 +209,10 @@ __device__ __forceinline__ void step_load(const KArgs& a, int i, typename Store<
 }
 
 template <int Q, int P, int L, int SK, bool FAST>
-__device__ __forceinline__ void step_store(const KArgs& a, int i, const typename Store<P>::R (&f)[Q]) {
+__device__ __forceinline__ void step_store(const KArgs& a, int i, const typename Store<P>::R (&f)[Q],
+                                           uint8_t fl = 0) {
   using R = typename Store<P>::R;
-  const Nb<FAST> nb(i, a);
+  const Nb<FAST> nb(i, a, fl);
   const int N = a.N;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -201,16 +221,16 @@ __device__ __forceinline__ void step_store(const KArgs& a, int i, const typename
       if constexpr (SK == K_TWOPOP) stp<P>(a.b, paddr<Q, L>(k, i, N), f[k]);
       else stp<P>(a.a, paddr<Q, L>(k, i, N), f[k]);
     } else {
-      const int wk = nb.template kind<Q, k>();
+      const bool bounce = nb.template solid<Q, k>();
       R v = f[k];
-      if (!FAST && wk != 0) v = v + R(__ldg(a.wall + wk * Q + k));
+      if (bounce) v = v + R(__ldg(a.wall + nb.template kind<Q, k>() * Q + k));
       if constexpr (SK == K_TWOPOP) {
-        if (wk == 0) stp<P>(a.b, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
+        if (!bounce) stp<P>(a.b, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
         else stp<P>(a.b, paddr<Q, L>(kb, i, N), v);
       } else if constexpr (SK == K_AA_EVEN) {
         stp<P>(a.a, paddr<Q, L>(kb, i, N), v);
       } else if constexpr (SK == K_AA_ODD) {
-        if (wk == 0) stp<P>(a.a, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
+        if (!bounce) stp<P>(a.a, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
         else stp<P>(a.a, paddr<Q, L>(kb, i, N), v);
       } else {  // esoteric twist
         const int cell = nb.template at<cneg<Q, k>(0), cneg<Q, k>(1), cneg<Q, k>(2)>();
@@ -249,12 +269,12 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i) {
     if (in_range) step_load<Q, P, L, SK, true>(a, i, f);
     fl = a.flags[i];
     if (fl & FLAG_KIND) return;  // solid cell: nothing to update
-    if (fl != 0) step_load<Q, P, L, SK, false>(a, i, f);
+    if (fl != 0) step_load<Q, P, L, SK, false>(a, i, f, fl);
   } else {
     fl = a.flags[i];
     if (fl & FLAG_KIND) return;
     if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
-    else step_load<Q, P, L, SK, false>(a, i, f);
+    else step_load<Q, P, L, SK, false>(a, i, f, fl);
   }
   CP<R> cp;
   cp.omega = R(a.omega);
@@ -265,7 +285,7 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i) {
   cp.trt_minus = R(a.trt_minus);
   collide<Q, M, R, Store<P>::shifted>(f, cp);
   if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
-  else step_store<Q, P, L, SK, false>(a, i, f);
+  else step_store<Q, P, L, SK, false>(a, i, f, fl);
 }
 
 // FP32/FP16 kernels of the light models are bound by memory latency: capping

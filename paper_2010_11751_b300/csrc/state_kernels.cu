@@ -10,7 +10,8 @@ namespace lbm {
 // flag classification: kind | FLAG_EDGE (domain face) | FLAG_NEARWALL
 // ---------------------------------------------------------------------------
 template <int Q>
-__global__ void classify_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out, int nx, int ny, int nz) {
+__global__ void classify_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
+                                uint32_t* __restrict__ mask_out, int nx, int ny, int nz) {
   const int N = nx * ny * nz;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -19,24 +20,28 @@ __global__ void classify_kernel(const uint8_t* __restrict__ raw, uint8_t* __rest
   uint8_t v = raw[i] & FLAG_KIND;
   if (v == 0) {
     if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1) v |= FLAG_EDGE;
-    bool near = false;
+    uint32_t mask = 0u;
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       int xn = x + Lat<Q>::c(k, 0), yn = y + Lat<Q>::c(k, 1), zn = z + Lat<Q>::c(k, 2);
       xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
       yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
       zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
-      if (raw[(xn * ny + yn) * nz + zn] & FLAG_KIND) near = true;
+      if (raw[(xn * ny + yn) * nz + zn] & FLAG_KIND) mask |= 1u << k;
     });
-    if (near) v |= FLAG_NEARWALL;
+    if (mask) v |= FLAG_NEARWALL;
+    mask_out[i] = mask;
+  } else {
+    mask_out[i] = 0u;
   }
   out[i] = v;
 }
 
-cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, int nx, int ny, int nz, cudaStream_t s) {
+cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, uint32_t* mask, int nx, int ny, int nz,
+                            cudaStream_t s) {
   const int N = nx * ny * nz, t = 256, b = (N + t - 1) / t;
-  if (Q == 19) classify_kernel<19><<<b, t, 0, s>>>(raw, out, nx, ny, nz);
-  else classify_kernel<27><<<b, t, 0, s>>>(raw, out, nx, ny, nz);
+  if (Q == 19) classify_kernel<19><<<b, t, 0, s>>>(raw, out, mask, nx, ny, nz);
+  else classify_kernel<27><<<b, t, 0, s>>>(raw, out, mask, nx, ny, nz);
   return cudaGetLastError();
 }
 
@@ -47,7 +52,7 @@ template <int Q, int P, int L, int LD>
 __device__ __forceinline__ void load_canonical_f64(const KArgs& a, int i, uint8_t fl, double (&f)[Q]) {
   typename Store<P>::R r[Q];
   if (fl == 0) load_cell<Q, P, L, LD, true>(a, Nb<true>(i, a), a.a, r);
-  else load_cell<Q, P, L, LD, false>(a, Nb<false>(i, a), a.a, r);
+  else load_cell<Q, P, L, LD, false>(a, Nb<false>(i, a, fl), a.a, r);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr double w = WGT<Q, k>;
@@ -114,7 +119,7 @@ template <int Q, int P, int L, int LD>
 __device__ __forceinline__ void store_canonical(const KArgs& a, int i, uint8_t fl,
                                                 const typename Store<P>::R (&r)[Q]) {
   if (fl == 0) store_cell_canonical<Q, P, L, LD, true>(a, Nb<true>(i, a), a.a, r);
-  else store_cell_canonical<Q, P, L, LD, false>(a, Nb<false>(i, a), a.a, r);
+  else store_cell_canonical<Q, P, L, LD, false>(a, Nb<false>(i, a, fl), a.a, r);
 }
 
 template <int Q, int P, int L, int LD>
@@ -229,14 +234,14 @@ __global__ void reduce_final_kernel(const double* partials, int n, double* out) 
 // k over the first half (the other half is handled by the neighbours)
 // ---------------------------------------------------------------------------
 template <int Q, int P, int L, bool FAST>
-__device__ __forceinline__ void swap_cell(const KArgs& a, int i) {
+__device__ __forceinline__ void swap_cell(const KArgs& a, int i, uint8_t fl) {
   using S = typename Store<P>::S;
   S* pop = reinterpret_cast<S*>(a.a);
-  const Nb<FAST> nb(i, a);
+  const Nb<FAST> nb(i, a, fl);
   static_for<0, Lat<Q>::H>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int kb = Lat<Q>::opp(k);
-    if (nb.template kind<Q, k>() == 0) {
+    if (!nb.template solid<Q, k>()) {
       const size_t p0 = paddr<Q, L>(kb, i, a.N), p1 = paddr<Q, L>(k, nb.template idx<Q, k>(), a.N);
       const S t0 = pop[p0], t1 = pop[p1];
       pop[p0] = t1;
@@ -250,8 +255,8 @@ __global__ void __launch_bounds__(256) swap_stream_kernel(KArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   const uint8_t fl = a.flags[i];
-  if (fl == 0) swap_cell<Q, P, L, true>(a, i);
-  else if ((fl & FLAG_KIND) == 0) swap_cell<Q, P, L, false>(a, i);
+  if (fl == 0) swap_cell<Q, P, L, true>(a, i, fl);
+  else if ((fl & FLAG_KIND) == 0) swap_cell<Q, P, L, false>(a, i, fl);
 }
 
 // ---------------------------------------------------------------------------
