@@ -247,14 +247,15 @@ __host__ __device__ constexpr int shifted_index(int j, int by) {
 }
 
 // KIND 0: raw -> central (shift -u), 1: central -> raw (+u),
-//      2: monomial -> Hermite (x^2 -> x^2 - cs^2), 3: Hermite -> monomial
-template <int Q, int AX, int KIND, typename R>
+//      2: monomial -> Hermite (x^2 -> x^2 - cs^2), 3: Hermite -> monomial.
+// Only basis elements of total order <= MAXO are transformed.
+template <int Q, int AX, int KIND, typename R, int MAXO = 6>
 __device__ __forceinline__ void axis_pass(R (&X)[Q], R u) {
   const R cs2 = R(1.0 / 3.0);
   // exponent 2 first (reads the old exponent-1 and exponent-0 entries)
   static_for<0, Q>([&](auto jc) {
     constexpr int J = decltype(jc)::value;
-    if constexpr (basis_exp(Q, J, AX) == 2) {
+    if constexpr (basis_exp(Q, J, AX) == 2 && basis_order(Q, J) <= MAXO) {
       constexpr int J1 = shifted_index<Q, AX>(J, 1), J0 = shifted_index<Q, AX>(J, 2);
       if constexpr (KIND == 0) X[J] = X[J] - R(2) * u * X[J1] + u * u * X[J0];
       else if constexpr (KIND == 1) X[J] = X[J] + R(2) * u * X[J1] + u * u * X[J0];
@@ -265,7 +266,7 @@ __device__ __forceinline__ void axis_pass(R (&X)[Q], R u) {
   if constexpr (KIND <= 1) {
     static_for<0, Q>([&](auto jc) {
       constexpr int J = decltype(jc)::value;
-      if constexpr (basis_exp(Q, J, AX) == 1) {
+      if constexpr (basis_exp(Q, J, AX) == 1 && basis_order(Q, J) <= MAXO) {
         constexpr int J0 = shifted_index<Q, AX>(J, 1);
         if constexpr (KIND == 0) X[J] = X[J] - u * X[J0];
         else X[J] = X[J] + u * X[J0];
@@ -274,17 +275,19 @@ __device__ __forceinline__ void axis_pass(R (&X)[Q], R u) {
   }
 }
 
-template <int Q, int KIND, typename R>
+template <int Q, int KIND, typename R, int MAXO = 6>
 __device__ __forceinline__ void all_axes(R (&X)[Q], R ux, R uy, R uz) {
-  axis_pass<Q, 0, KIND>(X, ux);
-  axis_pass<Q, 1, KIND>(X, uy);
-  axis_pass<Q, 2, KIND>(X, uz);
+  axis_pass<Q, 0, KIND, R, MAXO>(X, ux);
+  axis_pass<Q, 1, KIND, R, MAXO>(X, uy);
+  axis_pass<Q, 2, KIND, R, MAXO>(X, uz);
 }
 
 // ---------------------------------------------------------------------------
 // relaxation of a moment vector (normalised by rho)
 // ---------------------------------------------------------------------------
-template <int Q, typename R>
+// HIGH_EQ: orders >= 3 are set to their equilibrium (the omega_high = 1 case,
+// where they need not have been computed)
+template <int Q, typename R, bool HIGH_EQ = false>
 __device__ __forceinline__ void relax(R (&X)[Q], const R (&Xeq)[Q], const CP<R>& p) {
   constexpr int jxx = basis_index(Q, 2, 0, 0), jyy = basis_index(Q, 0, 2, 0), jzz = basis_index(Q, 0, 0, 2);
   const R dx = X[jxx] - Xeq[jxx], dy = X[jyy] - Xeq[jyy], dz = X[jzz] - Xeq[jzz];
@@ -301,6 +304,8 @@ __device__ __forceinline__ void relax(R (&X)[Q], const R (&Xeq)[Q], const CP<R>&
       X[J] = X[J] - p.wplus * dz - p.wminus * (dx + dy);
     } else if constexpr (o == 2) {
       X[J] = X[J] - p.omega * (X[J] - Xeq[J]);
+    } else if constexpr (HIGH_EQ) {
+      X[J] = Xeq[J];
     } else {
       X[J] = X[J] - p.omega_high * (X[J] - Xeq[J]);
     }
@@ -502,10 +507,23 @@ struct MomState {
   R rho, drho, ux, uy, uz;
 };
 
-template <int Q, typename R, bool SH>
+// MAXO = 2: only the moments of order <= 2 are computed (from pair sums); the
+// others are left at zero for the caller to overwrite
+template <int Q, typename R, bool SH, int MAXO = 6>
 __device__ __forceinline__ void load_moments(const R (&f)[Q], MomState<Q, R, SH>& st) {
   R M[Q];
-  raw_moments<Q>(f, M);
+  if constexpr (MAXO >= 6) {
+    raw_moments<Q>(f, M);
+  } else {
+    constexpr int H = Lat<Q>::H;
+    R s[H], d[H];
+    pair_sums<Q>(f, s, d);
+    static_for<0, Q>([&](auto jc) {
+      constexpr int J = decltype(jc)::value;
+      if constexpr (basis_order(Q, J) <= MAXO) M[J] = raw_moment_pairs<Q, J>(s, d, f[H]);
+      else M[J] = R(0);
+    });
+  }
   st.drho = M[0];
   st.rho = SH ? R(1) + M[0] : M[0];
   const R inv = R(1) / st.rho;
@@ -513,6 +531,7 @@ __device__ __forceinline__ void load_moments(const R (&f)[Q], MomState<Q, R, SH>
     constexpr int J = decltype(jc)::value;
     constexpr double wm = weight_moment<Q>(J);
     if constexpr (J == 0) st.Mh[J] = R(1);
+    else if constexpr (basis_order(Q, J) > MAXO) st.Mh[J] = R(0);
     else if constexpr (SH && wm != 0.0) st.Mh[J] = (M[J] + R(wm)) * inv;
     else st.Mh[J] = M[J] * inv;
   });
@@ -581,29 +600,39 @@ __device__ __forceinline__ void collide_nw4(R (&f)[Q], const CP<R>& p) {
   });
 }
 
-template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_rm(R (&f)[Q], const CP<R>& p) {
+template <int Q, typename R, bool SH, bool HEQ>
+__device__ __forceinline__ void collide_rm_impl(R (&f)[Q], const CP<R>& p) {
   MomState<Q, R, SH> st;
-  load_moments<Q, R, SH>(f, st);
+  load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
   R E[Q];
   eq_raw<Q>(st.ux, st.uy, st.uz, E);
-  relax<Q>(st.Mh, E, p);
+  relax<Q, R, HEQ>(st.Mh, E, p);
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
-
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_hm(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_rm(R (&f)[Q], const CP<R>& p) {
+  if (p.omega_high == R(1)) collide_rm_impl<Q, R, SH, true>(f, p);
+  else collide_rm_impl<Q, R, SH, false>(f, p);
+}
+
+template <int Q, typename R, bool SH, bool HEQ>
+__device__ __forceinline__ void collide_hm_impl(R (&f)[Q], const CP<R>& p) {
   MomState<Q, R, SH> st;
-  load_moments<Q, R, SH>(f, st);
-  all_axes<Q, 2>(st.Mh, st.ux, st.uy, st.uz);  // monomial -> Hermite
+  load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
+  all_axes<Q, 2, R, HEQ ? 2 : 6>(st.Mh, st.ux, st.uy, st.uz);  // monomial -> Hermite
   R E[Q];
   static_for<0, Q>([&](auto jc) {
     constexpr int J = decltype(jc)::value;
     E[J] = uprod<Q, J>(st.ux, st.uy, st.uz);
   });
-  relax<Q>(st.Mh, E, p);
+  relax<Q, R, HEQ>(st.Mh, E, p);
   all_axes<Q, 3>(st.Mh, st.ux, st.uy, st.uz);  // Hermite -> monomial
   store_moments<Q, R, SH>(st.Mh, st, f);
+}
+template <int Q, typename R, bool SH>
+__device__ __forceinline__ void collide_hm(R (&f)[Q], const CP<R>& p) {
+  if (p.omega_high == R(1)) collide_hm_impl<Q, R, SH, true>(f, p);
+  else collide_hm_impl<Q, R, SH, false>(f, p);
 }
 
 // central-moment equilibrium prod k_p, k = (1, 0, cs2)
@@ -616,41 +645,51 @@ __device__ __forceinline__ void eq_central(R (&E)[Q]) {
   });
 }
 
-template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_cm(R (&f)[Q], const CP<R>& p) {
+template <int Q, typename R, bool SH, bool HEQ>
+__device__ __forceinline__ void collide_cm_impl(R (&f)[Q], const CP<R>& p) {
   MomState<Q, R, SH> st;
-  load_moments<Q, R, SH>(f, st);
+  load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
-  all_axes<Q, 0>(st.Mh, ux, uy, uz);  // raw -> central
+  all_axes<Q, 0, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // raw -> central
   R E[Q];
   eq_central<Q>(E);
-  relax<Q>(st.Mh, E, p);
+  relax<Q, R, HEQ>(st.Mh, E, p);
   all_axes<Q, 1>(st.Mh, ux, uy, uz);  // central -> raw
   st.Mh[1] = ux;
   st.Mh[2] = uy;
   st.Mh[3] = uz;
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
-
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_chm(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_cm(R (&f)[Q], const CP<R>& p) {
+  if (p.omega_high == R(1)) collide_cm_impl<Q, R, SH, true>(f, p);
+  else collide_cm_impl<Q, R, SH, false>(f, p);
+}
+
+template <int Q, typename R, bool SH, bool HEQ>
+__device__ __forceinline__ void collide_chm_impl(R (&f)[Q], const CP<R>& p) {
   MomState<Q, R, SH> st;
-  load_moments<Q, R, SH>(f, st);
+  load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
-  all_axes<Q, 0>(st.Mh, ux, uy, uz);  // raw -> central
-  all_axes<Q, 2>(st.Mh, ux, uy, uz);  // central monomial -> central Hermite
+  all_axes<Q, 0, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // raw -> central
+  all_axes<Q, 2, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // central monomial -> central Hermite
   R E[Q];
   static_for<0, Q>([&](auto jc) {
     constexpr int J = decltype(jc)::value;
     E[J] = J == 0 ? R(1) : R(0);
   });
-  relax<Q>(st.Mh, E, p);
+  relax<Q, R, HEQ>(st.Mh, E, p);
   all_axes<Q, 3>(st.Mh, ux, uy, uz);  // central Hermite -> central monomial
   all_axes<Q, 1>(st.Mh, ux, uy, uz);  // central -> raw
   st.Mh[1] = ux;
   st.Mh[2] = uy;
   st.Mh[3] = uz;
   store_moments<Q, R, SH>(st.Mh, st, f);
+}
+template <int Q, typename R, bool SH>
+__device__ __forceinline__ void collide_chm(R (&f)[Q], const CP<R>& p) {
+  if (p.omega_high == R(1)) collide_chm_impl<Q, R, SH, true>(f, p);
+  else collide_chm_impl<Q, R, SH, false>(f, p);
 }
 
 // cumulants of orders 4..6 from normalised central moments (lower orders
@@ -695,13 +734,13 @@ __device__ __forceinline__ void cumulant_high(R (&X)[Q]) {
 #undef IX
 }
 
-template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_k(R (&f)[Q], const CP<R>& p) {
+template <int Q, typename R, bool SH, bool HEQ>
+__device__ __forceinline__ void collide_k_impl(R (&f)[Q], const CP<R>& p) {
   MomState<Q, R, SH> st;
-  load_moments<Q, R, SH>(f, st);
+  load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
-  all_axes<Q, 0>(st.Mh, ux, uy, uz);  // raw -> central
-  cumulant_high<Q, true>(st.Mh);      // central -> cumulant
+  all_axes<Q, 0, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // raw -> central
+  if constexpr (!HEQ) cumulant_high<Q, true>(st.Mh);   // central -> cumulant (orders 4..6)
   R E[Q];
   static_for<0, Q>([&](auto jc) {
     constexpr int J = decltype(jc)::value;
@@ -709,13 +748,18 @@ __device__ __forceinline__ void collide_k(R (&f)[Q], const CP<R>& p) {
     constexpr bool diag2 = o == 2 && (basis_exp(Q, J, 0) == 2 || basis_exp(Q, J, 1) == 2 || basis_exp(Q, J, 2) == 2);
     E[J] = J == 0 ? R(1) : (diag2 ? R(1.0 / 3.0) : R(0));
   });
-  relax<Q>(st.Mh, E, p);
+  relax<Q, R, HEQ>(st.Mh, E, p);
   cumulant_high<Q, false>(st.Mh);     // cumulant -> central
   all_axes<Q, 1>(st.Mh, ux, uy, uz);  // central -> raw
   st.Mh[1] = ux;
   st.Mh[2] = uy;
   st.Mh[3] = uz;
   store_moments<Q, R, SH>(st.Mh, st, f);
+}
+template <int Q, typename R, bool SH>
+__device__ __forceinline__ void collide_k(R (&f)[Q], const CP<R>& p) {
+  if (p.omega_high == R(1)) collide_k_impl<Q, R, SH, true>(f, p);
+  else collide_k_impl<Q, R, SH, false>(f, p);
 }
 
 // Recursive regularized (Hermite form): second-order non-equilibrium Hermite

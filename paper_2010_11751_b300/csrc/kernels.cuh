@@ -292,9 +292,11 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i) {
 // registers so that six (D3Q19) or four (D3Q27) 256-thread blocks fit per SM
 // measured fastest.  The moment models would spill under such caps, and FP64
 // kernels are bound by the FP64 pipe: both keep the default register budget.
+// FP64 kernels are capped at two blocks per SM (<= 128 registers) so that a
+// few warps per scheduler hide the FP64 pipe latency.
 template <int Q, int M, int P>
 inline constexpr int MIN_BLOCKS =
-    (P == F64 || !(M == BGK_W2 || M == TRT || M == REG)) ? 1 : (Q == 19 ? 6 : 4);
+    P == F64 ? 2 : (!(M == BGK_W2 || M == TRT || M == REG) ? 1 : (Q == 19 ? 6 : 4));
 // threads per block of the single-lattice step kernels
 inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }
 

@@ -184,3 +184,16 @@ def test_state_errors():
         with pytest.raises(L.LBMError) as ei:
             L.lbm_set_layout(g.h, L.AOS) or L.lbm_set_precision(g.h, L.F32)
         assert ei.value.code == L.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("model", ["RM", "HM", "CM", "CHM", "K"])
+@pytest.mark.parametrize("omega_bulk", [None, 1.1])
+def test_omega_high_one_path_matches_oracle(Q, model, omega_bulk):
+    """With omega_high = 1 (the default) the moment models skip the high-order moments
+    altogether (they relax to equilibrium); the result must still match the oracle."""
+    p = prm(omega=1.45, omega_bulk=1.45 if omega_bulk is None else omega_bulk, omega_high=1.0)
+    flags, f0 = case(Q, DIMS, seed=131, model=model)
+    ref = oracle_run(Q, DIMS, flags, model, p, f0, 6)
+    got = gpu_run(Q, DIMS, flags, model, p, f0, 6, scheme="aa")
+    assert rel_err(got, ref.f, flags) <= RTOL_F64
