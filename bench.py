@@ -39,6 +39,23 @@ FALLBACK_HBM_GBS = 6400.0
 FP64_FLOPS_PER_FLUID_CELL = {(19, "BGK_W2"): 182.2}
 # B300 FP64 pipe: 2 DFMA per SM per clock (ncu peak_sustained 296 thread-DFMA/cycle for 148 SMs)
 FP64_DFMA_PER_CLK = 296
+# DRAM bytes (read + write) per launch of the dominant step kernel, from one ncu capture
+# (profiles/*.md).  Reported only while the kernel sources hash to the value recorded with the
+# capture; any later kernel change turns the figure back to null.
+KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh"]
+TRAFFIC = {
+    # (precision, lattice, collision, scheme, n): (bytes per AA-odd launch, source hash)
+    ("f64", 19, "BGK_W2", "aa", 256): (2545943040 + 2448648704, "a711a2081aaf5c8d"),
+}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_11751_b300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -505,6 +522,10 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
+    tr = TRAFFIC.get((args.precision, args.lattice, args.collision, args.scheme, args.n))
+    if tr is not None and tr[1] == kernel_source_hash():
+        roof["traffic"] = tr[0]
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/)"
     roof["kernel"] = f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else "")
     roof["bytes_per_cell_update"] = r["bpc"]
     line = {
