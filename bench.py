@@ -158,6 +158,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, device):
+    """Slowest rank's value (the timing rule: the job is as fast as its slowest replica)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(world, cells_per_rank, steps, max_ms):
+    """Whole-job throughput: all ranks' cell updates over the slowest rank's time."""
+    return world * cells_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,10 +214,7 @@ def time_native(args, rank, local, pg):
     per = [evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
     if pg is not None:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
     m, e = g.reduce()
     bpc = g.bytes_per_cell_update
     # step kinds alternate for AA (even: local, odd: neighbour pull/push); the first timed
@@ -504,7 +516,7 @@ def main():
         return
     hbm, src = peaks()
     N, K = r["N"], args.steps
-    value = world * N * K / (r["total_ms"] * 1e-3) / 1e6
+    value = aggregate_mlups(world, N, K, r["total_ms"])
     dominant = r["odd"] if (args.scheme == "aa" and r["odd"]) else r["per"]
     dom_ms = sum(dominant) / len(dominant)
     achieved = r["bpc"] * N / (dom_ms * 1e-3) / 1e9
