@@ -99,6 +99,13 @@ def workload(args):
     return n, omega, I.cavity_flags(n, n, n), {I.LID: (0.02, 0.0, 0.0)}
 
 
+def config_dict(args, world):
+    return {"workload": workload_name(args), "lattice": f"D3Q{args.lattice}", "n": args.n,
+            "scheme": args.scheme, "layout": "soa", "collision": args.collision, "reynolds": args.reynolds,
+            "parallelism": f"replicas x{world}",
+            "l2": "no flush: population state larger than L2 (inputs larger than L2)"}
+
+
 def workload_name(args):
     return (f"D3Q{args.lattice} lid-driven cavity {args.n}^3 {args.precision.upper()}, Re {args.reynolds:g}, "
             f"{args.scheme} scheme, SoA, {args.collision}")
@@ -477,8 +484,43 @@ def serving_form(args):
     return out
 
 
+def size_sweep(args):
+    """Performance against domain size (the paper's N-dependence study, Section 3.3.3): D3Q19
+    cavity N^3 for N = 16..320, AA and two-population, BGK-W2 and RR, at the given precision."""
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    rows = []
+    for n in (16, 24, 32, 48, 64, 96, 128, 160, 192, 224, 256, 320):
+        args.n = n
+        _, omega, flags, walls = workload(args)
+        for scheme in ("aa", "twopop"):
+            for coll in ("BGK_W2", "RR"):
+                stream = torch.cuda.Stream()
+                g = L.Lattice(19, n, n, n, scheme, coll, omega, flags, precision=L.PRECISIONS[args.precision],
+                              wall_velocities=walls, stream=stream.cuda_stream)
+                g.init_equilibrium()
+                steps = max(4, min(200, int(2e9 // n ** 3)))
+                g.step(4)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                g.step(steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                rows.append({"n": n, "scheme": scheme, "collision": coll, "steps": steps,
+                             "mlups": round(n ** 3 / (ms * 1e-3) / 1e6, 1)})
+                g.close()
+    return rows
+
+
 def main():
     args = parse()
+    if args.forms == "sweep":
+        print(json.dumps({"form": "size_sweep", "precision": args.precision, "rows": size_sweep(args)}))
+        return
     if args.forms == "serving":
         print(json.dumps({"form": "serving", "config": f"{args.trace} requests, Poisson {args.rate:g}/s and "
                           f"{0.2 * args.rate:g}/s, side U[32,192], 100-2000 steps, D3Q19/D3Q27, cavity/TG, BGK/K, "
@@ -501,10 +543,9 @@ def main():
         W = args.warmup
         base, steps, t = oracle_baseline(args, 1e30, max_steps=args.steps, warmup=W)
         line = {"impl": "reference", "metric": f"MLUPS ({workload_name(args)})", "value": base["value"],
-                "unit": "MLUPS", "n_gpus": 0, "steps": steps, "warmup": W, "ms_per_step": round(1e3 * t / steps, 3),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": workload_name(args), "lattice": f"D3Q{args.lattice}",
-                                                "n": args.n, "collision": args.collision},
+                "unit": "MLUPS", "n_gpus": world, "steps": steps, "warmup": W,
+                "ms_per_step": round(1e3 * t / steps, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic", "config": config_dict(args, world),
                 "cpu_baseline": {"value": base["value"], "unit": "MLUPS", "cores": base["cores"], "kind": "oracle",
                                  "sample": base["sample"]},
                 "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -553,10 +594,7 @@ def main():
         "vs_baseline": None,
         "dtype": args.precision,
         "data": "synthetic",
-        "config": {"workload": workload_name(args), "lattice": f"D3Q{args.lattice}", "n": args.n,
-                   "scheme": args.scheme, "layout": "soa", "collision": args.collision, "reynolds": args.reynolds,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "no flush: population state larger than L2 (inputs larger than L2)"},
+        "config": config_dict(args, world),
         "roofline": roof,
         "hbm_frac_step": round(r["bpc"] * N * K / (r["total_ms"] * 1e-3) / 1e9 / hbm, 4),
         "gpu_launches": r["launches"],

@@ -197,3 +197,24 @@ def test_omega_high_one_path_matches_oracle(Q, model, omega_bulk):
     ref = oracle_run(Q, DIMS, flags, model, p, f0, 6)
     got = gpu_run(Q, DIMS, flags, model, p, f0, 6, scheme="aa")
     assert rel_err(got, ref.f, flags) <= RTOL_F64
+
+
+@pytest.mark.parametrize("scheme", ["twopop", "aa"])
+def test_divergence_is_reported(scheme):
+    """A non-finite population (injected through the host input, no device fault) spreads
+    through the collision and is reported by the FP64 conserved sums as LBM_ERR_DIVERGED."""
+    Q = 19
+    flags, f0 = case(Q, DIMS, seed=141)
+    bad = f0.copy()
+    i = int(np.flatnonzero(flags == 0)[7])
+    bad[3, i] = np.nan
+    with gpu_lattice(Q, DIMS, flags, "BGK_W2", prm(), scheme) as g:
+        g.set_populations(bad)
+        g.step(2)
+        with pytest.raises(L.LBMError) as ei:
+            g.reduce()
+        assert ei.value.code == L.ERR_DIVERGED
+    with gpu_lattice(Q, DIMS, flags, "BGK_W2", prm(), scheme) as g:
+        g.set_populations(f0)
+        g.step(2)
+        g.reduce()  # finite state: no error
