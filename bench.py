@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--trace", type=int, default=500, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrival rate (1/s)")
     ap.add_argument("--tick", type=int, default=64, help="serving: steps per tick")
+    ap.add_argument("--slot-cells", type=int, default=1 << 26, help="serving: active-cell budget")
     return ap.parse_args()
 
 
@@ -469,9 +470,11 @@ def serving_form(args):
     out = []
     for rate in (args.rate, 0.2 * args.rate):
         trace = trace_requests(I.serving_trace(args.trace, rate), reynolds=100.0)
-        for mode, limit in (("continuous_batching", None), ("fifo_queue_one_at_a_time", 1)):
+        for mode, limit, budget in (("continuous_batching", None, args.slot_cells),
+                                    ("fifo_queue_one_at_a_time", 1, None)):
             be = GpuBackend()
-            sched = Scheduler(be, tick_steps=args.tick, reserve_bytes=8 << 30, max_active=limit)
+            sched = Scheduler(be, tick_steps=args.tick, reserve_bytes=8 << 30, max_active=limit,
+                              max_active_cells=budget)
             t0 = time.perf_counter()
             res = sched.run(trace)
             wall = time.perf_counter() - t0
@@ -479,6 +482,7 @@ def serving_form(args):
             torch.cuda.empty_cache()
             s = summarize(res, wall)
             s.update({"mode": mode, "rate_hz": rate, "ticks": sched.ticks, "max_active": sched.max_active,
+                      "slot_cells": budget,
                       "offered_cell_updates": sum(r.side ** 3 * r.steps for r in trace)})
             out.append(s)
     return out

@@ -2,9 +2,10 @@
 //
 // A batch schedules member handles (same lattice, collision and precision,
 // AA pattern, SoA) with one kernel launch per time step covering all of them.
-// Per call, the member table (pointers, sizes, rates, step parity) is
-// uploaded; the block -> member map is rebuilt only when the membership or
-// the launch shape changes.  With use_graph, the n launches of a call are
+// Per call, the member table (pointers, sizes, rates) is uploaded; members are
+// split by step parity into two classes, each with its own block -> member
+// map, rebuilt only when the membership, the launch shape or the split
+// changes (a uniform parity flip just swaps the two classes).  With use_graph, the n launches of a call are
 // captured once into a CUDA graph and replayed while nothing changes.  The
 // autotuner times every (threads per block, cells per thread) pair on the
 // batch itself and caches the winner per (lattice, model, precision, size
@@ -35,13 +36,17 @@ struct lbm_batch_s {
   std::vector<Member> h_members;
   Member* d_members = nullptr;
   int cap_members = 0;
-  std::vector<int> h_map;
-  int* d_map = nullptr;
-  int cap_map = 0;
-  int blocks = 0;
+  // per parity class c (members whose step count had parity c when the maps were
+  // built): block -> member map on the device and its number of blocks
+  std::vector<int> h_map[2];
+  int* d_map[2] = {nullptr, nullptr};
+  int cap_map[2] = {0, 0};
+  int blocks[2] = {0, 0};
+  std::vector<int> map_parity;  // each member's step parity when the maps were built
   bool map_dirty = true;
   cudaGraphExec_t gexec = nullptr;
   int graph_n = 0;
+  int graph_e0 = 0;
   BatchFn fn = nullptr;
 };
 
@@ -67,31 +72,49 @@ void drop_graph(lbm_batch_s* b) {
 
 int rebuild_map(lbm_batch_s* b) {
   const int chunk = b->threads * b->cpt;
-  std::vector<int> begin(b->members.size());
-  int blocks = 0;
-  for (size_t m = 0; m < b->members.size(); ++m) {
-    begin[m] = blocks;
-    blocks += (b->members[m]->N + chunk - 1) / chunk;
+  const size_t n = b->members.size();
+  b->h_members.resize(n);
+  b->map_parity.resize(n);
+  for (int c = 0; c < 2; ++c) {
+    b->h_map[c].clear();
+    int blocks = 0;
+    for (size_t m = 0; m < n; ++m) {
+      const int par = (int)(b->members[m]->steps & 1);
+      b->map_parity[m] = par;
+      if (par != c) continue;
+      const int nb = (b->members[m]->N + chunk - 1) / chunk;
+      b->h_members[m].block_begin = blocks;
+      b->h_map[c].insert(b->h_map[c].end(), nb, (int)m);
+      blocks += nb;
+    }
+    if (blocks > b->cap_map[c]) {
+      if (b->d_map[c]) BCUDA(cudaFree(b->d_map[c]));
+      b->d_map[c] = nullptr;
+      BCUDA(cudaMalloc(&b->d_map[c], sizeof(int) * std::max(blocks, 1)));
+      b->cap_map[c] = blocks;
+    }
+    if (blocks)
+      BCUDA(cudaMemcpyAsync(b->d_map[c], b->h_map[c].data(), sizeof(int) * blocks, cudaMemcpyHostToDevice,
+                            bstream(b)));
+    b->blocks[c] = blocks;
   }
-  b->h_map.resize(blocks);
-  for (size_t m = 0; m < b->members.size(); ++m) {
-    const int nb = (b->members[m]->N + chunk - 1) / chunk;
-    std::fill(b->h_map.begin() + begin[m], b->h_map.begin() + begin[m] + nb, (int)m);
-  }
-  if (blocks > b->cap_map) {
-    if (b->d_map) BCUDA(cudaFree(b->d_map));
-    b->d_map = nullptr;
-    BCUDA(cudaMalloc(&b->d_map, sizeof(int) * std::max(blocks, 1)));
-    b->cap_map = blocks;
-  }
-  if (blocks) BCUDA(cudaMemcpyAsync(b->d_map, b->h_map.data(), sizeof(int) * blocks, cudaMemcpyHostToDevice, bstream(b)));
   BCUDA(cudaStreamSynchronize(bstream(b)));
-  b->blocks = blocks;
-  b->h_members.resize(b->members.size());
-  for (size_t m = 0; m < b->members.size(); ++m) b->h_members[m].block_begin = begin[m];
   b->map_dirty = false;
   drop_graph(b);
   return LBM_OK;
+}
+
+// which map holds the members of current parity 0: 0 or 1 (-1: the split changed)
+int parity_class_of_even(const lbm_batch_s* b) {
+  bool same = true, flipped = true;
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    const int par = (int)(b->members[m]->steps & 1);
+    same = same && par == b->map_parity[m];
+    flipped = flipped && par != b->map_parity[m];
+  }
+  if (same) return 0;
+  if (flipped) return 1;
+  return -1;
 }
 
 int upload_members(lbm_batch_s* b) {
@@ -111,7 +134,6 @@ int upload_members(lbm_batch_s* b) {
     d.ny = h->ny;
     d.nz = h->nz;
     d.N = h->N;
-    d.parity0 = (int)(h->steps & 1);
     handle_rates(h, &d.omega, &d.omc, &d.wplus, &d.wminus, &d.omega_high, &d.trt_minus);
   }
   if (n > b->cap_members) {
@@ -125,36 +147,43 @@ int upload_members(lbm_batch_s* b) {
   return LBM_OK;
 }
 
-cudaError_t launch_steps(lbm_batch_s* b, int n, cudaStream_t s) {
+// n steps; e0 = map class holding the members whose parity is 0 at the first step
+cudaError_t launch_steps(lbm_batch_s* b, int n, int e0, cudaStream_t s) {
   BatchArgs a;
   a.m = b->d_members;
-  a.block_member = b->d_map;
   a.cpt = b->cpt;
   for (int st = 0; st < n; ++st) {
-    a.step = st;
-    cudaError_t e = b->fn(a, b->blocks, b->threads, s);
-    if (e != cudaSuccess) return e;
+    const int ce = (e0 + st) & 1;  // class taking an even (local) step now
+    for (int c = 0; c < 2; ++c) {
+      if (!b->blocks[c]) continue;
+      a.block_member = b->d_map[c];
+      cudaError_t e = b->fn(a, c == ce ? K_AA_EVEN : K_AA_ODD, b->blocks[c], b->threads, s);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
 
 int run_steps(lbm_batch_s* b, int n, bool use_graph) {
   if (b->members.empty() || n == 0) return LBM_OK;
+  int rc;
+  if (!b->map_dirty && parity_class_of_even(b) < 0) b->map_dirty = true;
   if (b->map_dirty) {
-    int rc = rebuild_map(b);
+    rc = rebuild_map(b);
     if (rc) return rc;
   }
-  int rc = upload_members(b);
+  const int e0 = parity_class_of_even(b);
+  rc = upload_members(b);
   if (rc) return rc;
   cudaStream_t s = bstream(b);
   if (!use_graph) {
-    BCUDA(launch_steps(b, n, s));
+    BCUDA(launch_steps(b, n, e0, s));
   } else {
-    if (!b->gexec || b->graph_n != n) {
+    if (!b->gexec || b->graph_n != n || b->graph_e0 != e0) {
       drop_graph(b);
       cudaGraph_t g = nullptr;
       BCUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = launch_steps(b, n, s);
+      cudaError_t e = launch_steps(b, n, e0, s);
       cudaError_t e2 = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -164,6 +193,7 @@ int run_steps(lbm_batch_s* b, int n, bool use_graph) {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
       b->graph_n = n;
+      b->graph_e0 = e0;
     }
     BCUDA(cudaGraphLaunch(b->gexec, s));
   }
@@ -334,7 +364,8 @@ int lbm_batch_destroy(lbm_batch_t b) {
   cudaStreamSynchronize(bstream(b));
   drop_graph(b);
   if (b->d_members) cudaFree(b->d_members);
-  if (b->d_map) cudaFree(b->d_map);
+  for (int c = 0; c < 2; ++c)
+    if (b->d_map[c]) cudaFree(b->d_map[c]);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   delete b;
   return LBM_OK;

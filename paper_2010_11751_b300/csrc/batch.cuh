@@ -2,11 +2,12 @@
 //
 // Each member lattice keeps its own population array (AA pattern, SoA), flags,
 // wall table, relaxation rates and time-step parity.  A device table of member
-// descriptors and a block -> member map let one grid cover every member: a
-// block reads its member with one load, then updates threads x cells-per-thread
-// consecutive cells of that member with the same per-cell code as the
-// single-lattice kernels (so a batched step is bit-identical to stepping the
-// members one by one).
+// descriptors and, per step parity, a block -> member map let one grid cover
+// every member of that parity: a block reads its member with one load, then
+// updates threads x cells-per-thread consecutive cells of that member with the
+// same per-cell code as the single-lattice kernels (so a batched step is
+// bit-identical to stepping the members one by one).  A time step launches the
+// even-step kernel on one parity class and the odd-step kernel on the other.
 #pragma once
 #include "kernels.cuh"
 
@@ -18,26 +19,31 @@ struct __align__(16) Member {
   const uint32_t* nbmask;
   const double* wall;
   int nx, ny, nz, N;
-  int parity0;      // parity of the member's step count when the batch call starts
-  int block_begin;  // first grid block of the member
+  int pad_parity;   // unused
+  int block_begin;  // first grid block of the member (within its parity class map)
   int pad0, pad1;
   double omega, omc, wplus, wminus, omega_high, trt_minus;
 };
 
 struct BatchArgs {
   const Member* m;
-  const int* block_member;  // grid block -> member index
-  int step;                 // step index within the batch call (parity offset)
+  const int* block_member;  // grid block -> member index (members of one step parity)
   int cpt;                  // cells per thread
 };
 
-// the batch kernel holds both AA bodies and the cells-per-thread loop; register
-// caps that suit the single-lattice kernels make it spill, so it keeps the
-// default register budget
+// one kernel per AA step kind (SK = K_AA_EVEN or K_AA_ODD), so that each holds
+// a single body and takes the register bounds of the single-lattice kernels;
+// the host launches it on the members whose step parity matches
+// register bounds of the batch kernels: milder than the single-lattice ones,
+// because the member's pointers, sizes and rates come from a table in global
+// memory and live in registers (a single-lattice kernel reads them from its
+// launch parameters); chosen so that no variant spills
 template <int Q, int M, int P>
-inline constexpr int BATCH_MIN_BLOCKS = 1;
+inline constexpr int BATCH_MIN_BLOCKS =
+    P == F64 ? ((M == TRT && Q == 27) ? 1 : 2)
+             : (MIN_BLOCKS<Q, M, P> == 1 ? 1 : (Q == 19 ? 4 : 3));
 
-template <int Q, int M, int P>
+template <int Q, int M, int P, int SK>
 __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kernel(BatchArgs b) {
   const int mi = __ldg(b.block_member + blockIdx.x);
   const Member* mm = b.m + mi;
@@ -51,33 +57,30 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   a.ny = mm->ny;
   a.nz = mm->nz;
   a.N = mm->N;
-  a.omega = mm->omega;
-  a.omc = mm->omc;
-  a.wplus = mm->wplus;
-  a.wminus = mm->wminus;
-  a.omega_high = mm->omega_high;
-  a.trt_minus = mm->trt_minus;
-  const int parity = (mm->parity0 + b.step) & 1;
-  a.parity = parity;
+  a.parity = SK == K_AA_ODD ? 1 : 0;
+  using R = typename Store<P>::R;
+  CP<R> cp;  // rates converted once per block, in the arithmetic type
+  cp.omega = R(mm->omega);
+  cp.omc = R(mm->omc);
+  cp.wplus = R(mm->wplus);
+  cp.wminus = R(mm->wminus);
+  cp.omega_high = R(mm->omega_high);
+  cp.trt_minus = R(mm->trt_minus);
   const int base = (blockIdx.x - mm->block_begin) * blockDim.x * b.cpt + threadIdx.x;
-  if (parity == 0) {
-    for (int j = 0; j < b.cpt; ++j) {
-      const int i = base + j * blockDim.x;
-      if (i < a.N) step_one<Q, M, P, SOA, K_AA_EVEN>(a, i);
-    }
-  } else {
-    for (int j = 0; j < b.cpt; ++j) {
-      const int i = base + j * blockDim.x;
-      if (i < a.N) step_one<Q, M, P, SOA, K_AA_ODD>(a, i);
-    }
+#pragma unroll 1
+  for (int j = 0; j < b.cpt; ++j) {
+    const int i = base + j * blockDim.x;
+    if (i < a.N) step_one<Q, M, P, SOA, SK>(a, i, [&] { return cp; });
   }
 }
 
-using BatchFn = cudaError_t (*)(const BatchArgs&, int blocks, int threads, cudaStream_t);
+// sk: K_AA_EVEN or K_AA_ODD
+using BatchFn = cudaError_t (*)(const BatchArgs&, int sk, int blocks, int threads, cudaStream_t);
 
 template <int Q, int M, int P>
-cudaError_t launch_batch(const BatchArgs& b, int blocks, int threads, cudaStream_t s) {
-  batch_aa_kernel<Q, M, P><<<blocks, threads, 0, s>>>(b);
+cudaError_t launch_batch(const BatchArgs& b, int sk, int blocks, int threads, cudaStream_t s) {
+  if (sk == K_AA_EVEN) batch_aa_kernel<Q, M, P, K_AA_EVEN><<<blocks, threads, 0, s>>>(b);
+  else batch_aa_kernel<Q, M, P, K_AA_ODD><<<blocks, threads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@ namespace lbm {
 struct KArgs;
 struct BatchArgs;
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
-using BatchFn = cudaError_t (*)(const BatchArgs&, int blocks, int threads, cudaStream_t);
+using BatchFn = cudaError_t (*)(const BatchArgs&, int sk, int blocks, int threads, cudaStream_t);
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);

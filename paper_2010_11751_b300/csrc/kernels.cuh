@@ -258,8 +258,24 @@ __host__ __device__ constexpr bool early_loads() {
   return P != F16 && SK != K_AA_ODD && SK != K_ESOTWIST;
 }
 
-template <int Q, int M, int P, int L, int SK>
-__device__ __forceinline__ void step_one(const KArgs& a, int i) {
+template <int P>
+__device__ __forceinline__ CP<typename Store<P>::R> rates(const KArgs& a) {
+  using R = typename Store<P>::R;
+  CP<R> cp;
+  cp.omega = R(a.omega);
+  cp.omc = R(a.omc);
+  cp.wplus = R(a.wplus);
+  cp.wminus = R(a.wminus);
+  cp.omega_high = R(a.omega_high);
+  cp.trt_minus = R(a.trt_minus);
+  return cp;
+}
+
+// rate_fn() yields the relaxation rates; it is called just before the
+// collision, so that a single-lattice kernel reads them from its launch
+// parameters without holding registers across the loads
+template <int Q, int M, int P, int L, int SK, class RateFn>
+__device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn) {
   using R = typename Store<P>::R;
   R f[Q];
   uint8_t fl;
@@ -276,13 +292,7 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i) {
     if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
     else step_load<Q, P, L, SK, false>(a, i, f, fl);
   }
-  CP<R> cp;
-  cp.omega = R(a.omega);
-  cp.omc = R(a.omc);
-  cp.wplus = R(a.wplus);
-  cp.wminus = R(a.wminus);
-  cp.omega_high = R(a.omega_high);
-  cp.trt_minus = R(a.trt_minus);
+  const CP<R> cp = rate_fn();
   collide<Q, M, R, Store<P>::shifted>(f, cp);
   if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
   else step_store<Q, P, L, SK, false>(a, i, f, fl);
@@ -296,7 +306,8 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i) {
 // few warps per scheduler hide the FP64 pipe latency.
 template <int Q, int M, int P>
 inline constexpr int MIN_BLOCKS =
-    P == F64 ? 2 : (!(M == BGK_W2 || M == TRT || M == REG) ? 1 : (Q == 19 ? 6 : 4));
+    P == F64 ? 2
+             : (!(M == BGK_W2 || M == TRT || M == REG) ? 1 : (Q == 19 ? (M == TRT ? 5 : 6) : 4));
 // threads per block of the single-lattice step kernels
 inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }
 
@@ -304,7 +315,7 @@ template <int Q, int M, int P, int L, int SK>
 __global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_kernel(KArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
-  step_one<Q, M, P, L, SK>(a, i);
+  step_one<Q, M, P, L, SK>(a, i, [&] { return rates<P>(a); });
 }
 
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);

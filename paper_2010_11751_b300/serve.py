@@ -66,9 +66,12 @@ class Scheduler:
     """FIFO admission by free device memory, ticks of grouped batched steps, harvesting."""
 
     def __init__(self, backend, tick_steps: int = 64, reserve_bytes: int = 0, clock=time.perf_counter,
-                 max_active: int | None = None):
+                 max_active: int | None = None, max_active_cells: int | None = None):
         self.backend = backend
         self.limit = max_active  # None: bounded by memory only; 1: a plain FIFO queue, one solve at a time
+        # slot budget in lattice cells: enough active work to saturate the GPU without letting
+        # every waiting request share it (which delays all completions); None: memory only
+        self.cell_budget = max_active_cells
         self.tick_steps = int(tick_steps)
         self.reserve = int(reserve_bytes)
         self.clock = clock
@@ -99,6 +102,9 @@ class Scheduler:
                 continue
             if need + self.reserve > self.backend.free_bytes():
                 break  # head of line waits for memory to free up
+            if self.cell_budget is not None and self.active:
+                if sum(a.req.side ** 3 for a in self.active) + req.side ** 3 > self.cell_budget:
+                    break  # head of line waits for a slot
             self.pending.popleft()
             h = self.backend.start(req)
             self.active.append(_Active(req, h, self.now()))

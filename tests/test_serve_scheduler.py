@@ -134,3 +134,19 @@ def test_queue_only_mode_runs_one_at_a_time():
     res = s.run([req(i, 4, 20, t=0.0) for i in range(4)], idle_sleep=0.0)
     assert s.max_active == 1 and [r.id for r in res] == [0, 1, 2, 3]
     assert all(len(ids) == 1 for _, ids, _ in be.steps)
+
+
+def test_cell_budget_slots():
+    be = FakeBackend(total=10 ** 9)
+    s = Scheduler(be, tick_steps=8, clock=Clock(), max_active_cells=2 * 64 + 10)
+    s.t0 = 0.0
+    for i in range(4):
+        s.offer(req(i, 4, 16))  # 64 cells each
+    assert s.admit() == [0, 1]  # the third would exceed the budget
+    while s.active:
+        s.tick()
+    assert s.admit() == [2, 3]
+    s2 = Scheduler(be, clock=Clock(), max_active_cells=10)
+    s2.t0 = 0.0
+    s2.offer(req(9, 4, 8))  # larger than the budget alone: still admitted when nothing is active
+    assert s2.admit() == [9]
