@@ -135,6 +135,8 @@ KArgs make_args(const lbm_s* h) {
   a.wplus = a.wminus + w;
   a.omega_high = h->omega_high;
   a.trt_minus = 1.0 / (0.5 + h->lambda / (1.0 / w - 0.5));
+  if (h->Q == 19) derived_rates<19>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+  else derived_rates<27>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
   return a;
 }
 

@@ -40,7 +40,7 @@ struct BatchArgs {
 // launch parameters); chosen so that no variant spills
 template <int Q, int M, int P>
 inline constexpr int BATCH_MIN_BLOCKS =
-    P == F64 ? ((M == TRT && Q == 27) ? 1 : 2)
+    P == F64 ? 2
              : (MIN_BLOCKS<Q, M, P> == 1 ? 1 : (Q == 19 ? 4 : 3));
 
 template <int Q, int M, int P, int SK>
@@ -66,6 +66,17 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   cp.wminus = R(mm->wminus);
   cp.omega_high = R(mm->omega_high);
   cp.trt_minus = R(mm->trt_minus);
+  {
+    double wt[4], wt3[4], wm3[4], hs, hd;
+    derived_rates<Q>(mm->omega, mm->trt_minus, wt, wt3, wm3, hs, hd);
+    for (int c = 0; c < 4; ++c) {
+      cp.wt[c] = R(wt[c]);
+      cp.wt3[c] = R(wt3[c]);
+      cp.wm3[c] = R(wm3[c]);
+    }
+    cp.hs = R(hs);
+    cp.hd = R(hd);
+  }
   const int base = (blockIdx.x - mm->block_begin) * blockDim.x * b.cpt + threadIdx.x;
 #pragma unroll 1
   for (int j = 0; j < b.cpt; ++j) {

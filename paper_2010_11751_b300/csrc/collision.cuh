@@ -31,7 +31,15 @@ struct CP {
   R wminus;     // bulk coupling w- = (w_b - w) / 3
   R omega_high; // rate of moments of order >= 3
   R trt_minus;  // TRT antisymmetric rate from Lambda
+  // per weight class c = |c_k|^2: w t_c, 3 w t_c and 3 w- t_c, with (1 - w)/2
+  // and (1 - w-)/2 (precomputed on the host for the single-lattice kernels, so
+  // that no thread spends FP64 operations on them)
+  R wt[4], wt3[4], wm3[4];
+  R hs, hd;
 };
+
+template <int Q, int K>
+inline constexpr int WCLASS = Lat<Q>::norm2(K);
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -364,42 +372,61 @@ __device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p) {
     jz = addc<Lat<Q>::e(k, 2)>(jz, d[k]);
   });
   const R rho = SH ? R(1) + r : r;
-  const R inv = R(1) / rho;
-  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  // A = rho (1 - 1.5 |u|^2) = rho - 1.5 u.j  (shifted: A - 1 = drho - 1.5 u.j)
-  const R uj = ux * jx + uy * jy + uz * jz;
-  const R A = r - R(1.5) * uj;
-  // FP64 relaxes as (1 - w) f + w E (one operation fewer per population on
-  // the FP64 pipe); FP32 relaxes in non-equilibrium form f + w (E - f), which
-  // keeps the rounding of the large terms out of the small non-equilibrium part
-  constexpr bool neq_form = !std::is_same<R, double>::value;
-  if constexpr (neq_form) f[H] = f[H] + p.omega * (R(WGT<Q, H>) * A - f[H]);
-  else f[H] = p.omc * f[H] + (p.omega * R(WGT<Q, H>)) * A;
-  static_for<0, H>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
-    R eu = R(-0.0), ej = R(-0.0);
-    eu = addc<ex>(eu, ux);
-    eu = addc<ey>(eu, uy);
-    eu = addc<ez>(eu, uz);
-    ej = addc<ex>(ej, jx);
-    ej = addc<ey>(ej, jy);
-    ej = addc<ez>(ej, jz);
-    // E_+- = t (A + 4.5 (e.u)(e.j) +- 3 e.j)
-    if constexpr (neq_form) {
+  if constexpr (std::is_same<R, double>::value) {
+    // FP64 is bound by the FP64 pipe, so the update is arranged for the fewest
+    // operations: with v = 1.5 u and q_k = 3 w t_k (e.j),
+    //   w E_+- = w t A + (e.v) q_k +- q_k,
+    // and relaxes as (1 - w) f + w E
+    // (explicit fma / rounded adds: the contraction of products into sums is
+    // fixed in the source, so that every kernel instantiating this update,
+    // single-lattice or batched, rounds identically)
+    const R inv15 = R(1.5) / rho;
+    const R vx = jx * inv15, vy = jy * inv15, vz = jz * inv15;
+    const R A = r - fma(vx, jx, fma(vy, jy, __dmul_rn(vz, jz)));  // rho (1 - 1.5 |u|^2) (shifted: minus 1)
+    f[H] = fma(p.omc, f[H], __dmul_rn(p.wt[0], A));
+    static_for<0, H>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
+      constexpr int c = WCLASS<Q, k>;
+      R ev = R(-0.0), ej = R(-0.0);
+      ev = addc<ex>(ev, vx);
+      ev = addc<ey>(ev, vy);
+      ev = addc<ez>(ev, vz);
+      ej = addc<ex>(ej, jx);
+      ej = addc<ey>(ej, jy);
+      ej = addc<ez>(ej, jz);
+      const R q = __dmul_rn(p.wt3[c], ej);
+      const R P = fma(ev, q, __dmul_rn(p.wt[c], A));
+      f[k + H + 1] = fma(p.omc, f[k + H + 1], __dadd_rn(P, q));
+      f[k] = fma(p.omc, f[k], __dsub_rn(P, q));
+    });
+  } else {
+    // FP32 / FP16 storage: relax in non-equilibrium form f + w (E - f), which
+    // keeps the rounding of the large terms out of the small non-equilibrium part
+    const R inv = R(1) / rho;
+    const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    // A = rho (1 - 1.5 |u|^2) = rho - 1.5 u.j  (shifted: A - 1 = drho - 1.5 u.j)
+    const R uj = ux * jx + uy * jy + uz * jz;
+    const R A = r - R(1.5) * uj;
+    f[H] = f[H] + p.omega * (R(WGT<Q, H>) * A - f[H]);
+    static_for<0, H>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
+      R eu = R(-0.0), ej = R(-0.0);
+      eu = addc<ex>(eu, ux);
+      eu = addc<ey>(eu, uy);
+      eu = addc<ez>(eu, uz);
+      ej = addc<ex>(ej, jx);
+      ej = addc<ey>(ej, jy);
+      ej = addc<ez>(ej, jz);
+      // E_+- = t (A + 4.5 (e.u)(e.j) +- 3 e.j)
       const R t = R(WGT<Q, k>);
       const R S = (R(4.5) * t * eu) * ej + t * A;
       const R T = (R(3) * t) * ej;
       f[k + H + 1] = f[k + H + 1] + p.omega * ((S + T) - f[k + H + 1]);
       f[k] = f[k] + p.omega * ((S - T) - f[k]);
-    } else {
-      const R W = p.omega * R(WGT<Q, k>);
-      const R S = (R(4.5) * W * eu) * ej + W * A;
-      const R T = (R(3) * W) * ej;
-      f[k + H + 1] = p.omc * f[k + H + 1] + (S + T);
-      f[k] = p.omc * f[k] + (S - T);
-    }
-  });
+    });
+  }
 }
 
 // TRT: symmetric part relaxes with w, antisymmetric part with w- (from Lambda).
@@ -419,28 +446,58 @@ __device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p) {
     jz = addc<Lat<Q>::e(k, 2)>(jz, d[k]);
   });
   const R rho = SH ? R(1) + r : r;
-  const R inv = R(1) / rho;
-  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  const R uj = ux * jx + uy * jy + uz * jz;
-  const R A = r - R(1.5) * uj;
-  f[H] = f[H] - p.omega * (f[H] - R(WGT<Q, H>) * A);
-  const R hp = R(0.5) * p.omega, hm = R(0.5) * p.trt_minus;
-  static_for<0, H>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
-    R eu = R(-0.0), ej = R(-0.0);
-    eu = addc<ex>(eu, ux);
-    eu = addc<ey>(eu, uy);
-    eu = addc<ez>(eu, uz);
-    ej = addc<ex>(ej, jx);
-    ej = addc<ey>(ej, jy);
-    ej = addc<ez>(ej, jz);
-    const R Sp = (R(4.5) * eu) * ej + A;
-    const R a = hp * s[k] - (p.omega * R(WGT<Q, k>)) * Sp;      // w+ (f+ - E+)
-    const R b = hm * d[k] - (R(3) * p.trt_minus * R(WGT<Q, k>)) * ej;  // w- (f-_plus - E-_plus)
-    f[k + H + 1] = f[k + H + 1] - a - b;
-    f[k] = f[k] - a + b;
-  });
+  if constexpr (std::is_same<R, double>::value) {
+    // fewest FP64 operations: with v = 1.5 u, w E+ = w t A + (e.v) q+ and
+    // w- E-_plus = q-, where q+ = 3 w t (e.j) and q- = 3 w- t (e.j); the pair is
+    // rebuilt from its symmetric and antisymmetric parts,
+    //   X = (1 - w) s/2 + w E+,  Y = (1 - w-) d/2 + w- E-_plus,
+    //   f_plus = X + Y,  f_minus = X - Y  (d = f_plus - f_minus, s = f_plus + f_minus)
+    // (explicit fma / rounded adds, as in BGK-W2)
+    const R inv15 = R(1.5) / rho;
+    const R vx = jx * inv15, vy = jy * inv15, vz = jz * inv15;
+    const R A = r - fma(vx, jx, fma(vy, jy, __dmul_rn(vz, jz)));
+    f[H] = fma(p.omc, f[H], __dmul_rn(p.wt[0], A));
+    static_for<0, H>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
+      constexpr int c = WCLASS<Q, k>;
+      R ev = R(-0.0), ej = R(-0.0);
+      ev = addc<ex>(ev, vx);
+      ev = addc<ey>(ev, vy);
+      ev = addc<ez>(ev, vz);
+      ej = addc<ex>(ej, jx);
+      ej = addc<ey>(ej, jy);
+      ej = addc<ez>(ej, jz);
+      const R qp = __dmul_rn(p.wt3[c], ej);
+      const R X = fma(p.hs, s[k], fma(ev, qp, __dmul_rn(p.wt[c], A)));
+      const R Y = fma(p.hd, d[k], __dmul_rn(p.wm3[c], ej));
+      f[k + H + 1] = X + Y;
+      f[k] = X - Y;
+    });
+  } else {
+    const R inv = R(1) / rho;
+    const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const R uj = ux * jx + uy * jy + uz * jz;
+    const R A = r - R(1.5) * uj;
+    f[H] = f[H] - p.omega * (f[H] - R(WGT<Q, H>) * A);
+    const R hp = R(0.5) * p.omega, hm = R(0.5) * p.trt_minus;
+    static_for<0, H>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
+      R eu = R(-0.0), ej = R(-0.0);
+      eu = addc<ex>(eu, ux);
+      eu = addc<ey>(eu, uy);
+      eu = addc<ez>(eu, uz);
+      ej = addc<ex>(ej, jx);
+      ej = addc<ey>(ej, jy);
+      ej = addc<ez>(ej, jz);
+      const R Sp = (R(4.5) * eu) * ej + A;
+      const R a = hp * s[k] - (p.omega * R(WGT<Q, k>)) * Sp;      // w+ (f+ - E+)
+      const R b = hm * d[k] - (R(3) * p.trt_minus * R(WGT<Q, k>)) * ej;  // w- (f-_plus - E-_plus)
+      f[k + H + 1] = f[k + H + 1] - a - b;
+      f[k] = f[k] - a + b;
+    });
+  }
 }
 
 // Regularized: f_out = E + (1 - w) t_k/(2 cs^4) H2_k : Pi_neq,

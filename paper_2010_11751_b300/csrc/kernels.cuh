@@ -45,7 +45,26 @@ struct KArgs {
   int nx, ny, nz, N;
   int parity;             // time-step parity (esoteric twist slot labels)
   double omega, omc, wplus, wminus, omega_high, trt_minus;
+  // per weight class c = |c|^2: w t_c, 3 w t_c, 3 w- t_c; and (1 - w)/2, (1 - w-)/2
+  double wt[4], wt3[4], wm3[4], hs, hd;
 };
+
+// rate constants derived from w and w- (host side, and once per block in the
+// batch kernels)
+template <int Q>
+__host__ __device__ inline void derived_rates(double omega, double trt_minus, double (&wt)[4], double (&wt3)[4],
+                                              double (&wm3)[4], double& hs, double& hd) {
+  for (int c = 0; c < 4; ++c) {
+    double t = 0.0;
+    for (int k = 0; k < Q; ++k)
+      if (Lat<Q>::norm2(k) == c) t = Lat<Q>::w(k);
+    wt[c] = omega * t;
+    wt3[c] = 3.0 * (omega * t);
+    wm3[c] = (3.0 * trt_minus) * t;
+  }
+  hs = 0.5 * (1.0 - omega);
+  hd = 0.5 * (1.0 - trt_minus);
+}
 
 // ---------------------------------------------------------------------------
 // population addressing
@@ -268,6 +287,13 @@ __device__ __forceinline__ CP<typename Store<P>::R> rates(const KArgs& a) {
   cp.wminus = R(a.wminus);
   cp.omega_high = R(a.omega_high);
   cp.trt_minus = R(a.trt_minus);
+  for (int c = 0; c < 4; ++c) {
+    cp.wt[c] = R(a.wt[c]);
+    cp.wt3[c] = R(a.wt3[c]);
+    cp.wm3[c] = R(a.wm3[c]);
+  }
+  cp.hs = R(a.hs);
+  cp.hd = R(a.hd);
   return cp;
 }
 
