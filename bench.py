@@ -33,19 +33,25 @@ from paper_2010_11751_b300 import inputs as I  # noqa: E402
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
-# FP64 flops executed per fluid-cell update by the step kernel (ncu: dadd + dmul + 2 dfma per
-# launch / fluid cells, D3Q19 cavity 128^3, both AA kernels identical); see
-# profiles/aa_step_d3q19_f64_bgk_128.md.  The FP64 kernels are bound by the FP64 pipe.
-FP64_FLOPS_PER_FLUID_CELL = {(19, "BGK_W2"): 182.2}
-# B300 FP64 pipe: 2 DFMA per SM per clock (ncu peak_sustained 296 thread-DFMA/cycle for 148 SMs)
-FP64_DFMA_PER_CLK = 296
+# FP64 operations executed per fluid-cell update by the AA step kernels (ncu: dadd, dmul and dfma
+# thread instructions per launch / fluid cells, D3Q19 cavity 128^3; the even and odd kernels
+# execute the same counts).  The FP64 kernels are bound by the FP64 pipe, which issues one
+# DADD, DMUL or DFMA per slot, so the roofline counts operations (flops are reported beside).
+FP64_OPS_PER_FLUID_CELL = {
+    # (lattice, collision): (dadd, dmul, dfma) per fluid cell
+    (19, "BGK_W2"): (70.24, 17.00, 37.00),
+    (19, "TRT"): (70.24, 26.00, 37.00),
+}
+# B300 FP64 pipe: 2 DFMA (or DADD / DMUL) per SM per clock (ncu peak_sustained: 296 thread
+# operations per cycle for 148 SMs)
+FP64_OPS_PER_CLK = 296
 # DRAM bytes (read + write) per launch of the dominant step kernel, from one ncu capture
 # (profiles/*.md).  Reported only while the kernel sources hash to the value recorded with the
 # capture; any later kernel change turns the figure back to null.
 KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh"]
 TRAFFIC = {
     # (precision, lattice, collision, scheme, n): (bytes per AA-odd launch, source hash)
-    ("f64", 19, "BGK_W2", "aa", 256): (2545943040 + 2448648704, "a711a2081aaf5c8d"),
+    ("f64", 19, "BGK_W2", "aa", 256): (2544815360 + 2448811264, "46b10fc809b204bf"),
 }
 
 
@@ -565,17 +571,20 @@ def main():
     dominant = r["odd"] if (args.scheme == "aa" and r["odd"]) else r["per"]
     dom_ms = sum(dominant) / len(dominant)
     achieved = r["bpc"] * N / (dom_ms * 1e-3) / 1e9
-    flops = FP64_FLOPS_PER_FLUID_CELL.get((args.lattice, args.collision)) if args.precision == "f64" else None
-    if flops is not None:
+    ops = FP64_OPS_PER_FLUID_CELL.get((args.lattice, args.collision)) if args.precision == "f64" else None
+    if ops is not None:
         fluid = (args.n - 2) ** 3
         clk = (r["clocks"].get("sm_max_mhz") or 2032.0) * 1e6
-        peak_tf = FP64_DFMA_PER_CLK * 2 * clk / 1e12
-        tf = flops * fluid / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(tf, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-                "frac": round(tf / peak_tf, 4), "traffic": None,
-                "peak_source": "derived: 2 DFMA/SM/clk x 148 SMs x max SM clock x 2 flops",
-                "flops_per_fluid_cell": flops, "hbm_achieved_gbs": round(achieved, 1),
-                "hbm_frac": round(achieved / hbm, 4)}
+        peak = FP64_OPS_PER_CLK * clk / 1e9
+        nops = sum(ops)
+        rate = nops * fluid / (dom_ms * 1e-3) / 1e9
+        flops = ops[0] + ops[1] + 2 * ops[2]
+        roof = {"bound": "alu", "achieved": round(rate, 1), "peak": round(peak, 1), "unit": "G FP64 op/s",
+                "frac": round(rate / peak, 4), "traffic": None,
+                "peak_source": "derived: 2 FP64 operations (DADD, DMUL or DFMA) per SM per clock x 148 SMs x max SM clock",
+                "fp64_ops_per_fluid_cell": round(nops, 2), "flops_per_fluid_cell": round(flops, 2),
+                "tflops": round(flops * fluid / (dom_ms * 1e-3) / 1e12, 4),
+                "hbm_achieved_gbs": round(achieved, 1), "hbm_frac": round(achieved / hbm, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
