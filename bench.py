@@ -236,7 +236,7 @@ def time_native(args, rank, local, pg):
     first = args.warmup % 2
     odd = [t for s, t in enumerate(per) if (first + s) % 2 == 1]
     even = [t for s, t in enumerate(per) if (first + s) % 2 == 0]
-    launches_per_step = 2 if args.scheme == "swap" else 1
+    launches_per_step = L.lbm_kernels_per_step(g.h)
     res = dict(N=N, total_ms=total_ms, per=per, odd=odd, even=even, bpc=bpc, mass=m, energy=e,
                clocks=clk.summary(), launches=args.steps * launches_per_step)
     g.close()

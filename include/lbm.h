@@ -168,6 +168,14 @@ LBM_API int lbm_device_bytes(lbm_t h, size_t* bytes);
  * read + written + the 1-byte cell flag), for roofline accounting. */
 LBM_API int lbm_bytes_per_cell_update(lbm_t h, double* bytes);
 
+/* Number of kernel launches one time step of the handle makes (*n >= 1):
+ * 1 for the one-thread-per-cell kernels; 2 for swap (collision, then the
+ * streaming pass) and for the staged AA steps of FP16 SoA storage (the
+ * shared-memory-staged kernel over the bulk cells, then the kernel over the
+ * cells next to a wall or on a domain face, if there are any).  May build the
+ * latter's cell list (device memory it owns; see lbm_device_bytes). */
+LBM_API int lbm_kernels_per_step(lbm_t h, int* n);
+
 /* Free everything the handle owns.  NULL is accepted. */
 LBM_API int lbm_destroy(lbm_t h);
 

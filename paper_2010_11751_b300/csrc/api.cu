@@ -73,6 +73,57 @@ size_t pop_bytes(const lbm_s* h) { return (size_t)h->Q * (size_t)h->N * elem_siz
 int resolve_kernels(lbm_s* h) {
   for (int sk = 0; sk < NUM_STEP_KINDS; ++sk) h->fns[sk] = step_fn(h->model, h->Q, h->prec, h->layout, sk);
   if (!h->fns[K_TWOPOP]) return fail(LBM_ERR_UNSUPPORTED, "combination of lattice, model, precision and layout is not built");
+  const bool staged = h->scheme == LBM_AA && h->layout == SOA;
+  h->sfns[0] = staged ? staged_fn(h->model, h->Q, h->prec, K_AA_EVEN) : nullptr;
+  h->sfns[1] = staged ? staged_fn(h->model, h->Q, h->prec, K_AA_ODD) : nullptr;
+  return LBM_OK;
+}
+
+KArgs make_args(const lbm_s* h);
+
+// sorted list of the fluid cells with a non-zero flag byte and its per-tile
+// offsets, built once per handle before the first staged step (the flags never
+// change after lbm_create)
+int ensure_nonbulk_list(lbm_s* h) {
+  if (h->nlist >= 0) return LBM_OK;
+  const int tile = staged_tile(h->Q);
+  const int ntiles = (h->N + tile - 1) / tile;
+  std::vector<int> off((size_t)ntiles + 1, 0);
+  LBM_CUDA(cudaMalloc(&h->d_tile_off, sizeof(int) * ((size_t)ntiles + 1)));
+  LBM_CUDA(launch_list_count(h->d_flags, h->N, tile, h->d_tile_off, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(off.data(), h->d_tile_off, sizeof(int) * (size_t)ntiles, cudaMemcpyDeviceToHost,
+                           h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  long long run = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    const int c = off[t];
+    off[t] = (int)run;
+    run += c;
+  }
+  off[ntiles] = (int)run;
+  LBM_CUDA(cudaMemcpyAsync(h->d_tile_off, off.data(), sizeof(int) * ((size_t)ntiles + 1), cudaMemcpyHostToDevice,
+                           h->stream));
+  if (run > 0) {
+    LBM_CUDA(cudaMalloc(&h->d_list, sizeof(int) * (size_t)run));
+    LBM_CUDA(cudaMalloc(&h->d_list_mask, sizeof(uint32_t) * (size_t)run));
+    LBM_CUDA(cudaMalloc(&h->d_list_kinds, 2 * sizeof(unsigned long long) * (size_t)run));
+    LBM_CUDA(launch_list_fill(h->d_flags, h->N, tile, h->d_tile_off, h->d_list, h->stream));
+    LBM_CUDA(launch_listed_records(h->Q, make_args(h), h->d_list, (int)run, h->d_list_mask, h->d_list_kinds,
+                                   h->stream));
+  }
+  LBM_CUDA(cudaStreamSynchronize(h->stream));  // `off` is read by the copy above
+  LBM_CUDA(cudaFree(h->d_tile_off));           // only needed to sort the list
+  h->d_tile_off = nullptr;
+  h->nlist = (int)run;
+  return LBM_OK;
+}
+
+// LBM_ERR_TIMEOUT if a staged kernel recorded a bounded wait that gave up
+// (reads the device error word; the caller has synchronised the stream)
+int check_device_error(lbm_s* h) {
+  int w = 0;
+  LBM_CUDA(cudaMemcpy(&w, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (w != 0) return fail(LBM_ERR_TIMEOUT, "a staged step kernel gave up waiting for its staged copies");
   return LBM_OK;
 }
 
@@ -85,8 +136,9 @@ int ensure_alloc(lbm_s* h) {
     return fail(LBM_ERR_OOM, "populations need " + std::to_string(need >> 20) + " MiB, " +
                                  std::to_string(freeb >> 20) + " MiB free");
   for (int a = 0; a < h->npop; ++a) {
-    LBM_CUDA(cudaMalloc(&h->d_pop[a], pop_bytes(h)));
-    LBM_CUDA(cudaMemsetAsync(h->d_pop[a], 0, pop_bytes(h), h->stream));
+    // the staged kernels copy whole 128-byte units, up to STAGE_PAD_BYTES past the end
+    LBM_CUDA(cudaMalloc(&h->d_pop[a], pop_bytes(h) + STAGE_PAD_BYTES));
+    LBM_CUDA(cudaMemsetAsync(h->d_pop[a], 0, pop_bytes(h) + STAGE_PAD_BYTES, h->stream));
   }
   return LBM_OK;
 }
@@ -239,7 +291,10 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
     return rc;
   }
   uint8_t* raw = nullptr;
-  cudaError_t e = cudaMalloc(&h->d_flags, N);
+  cudaError_t e = cudaMalloc(&h->d_flags, N + STAGE_PAD_BYTES);  // padded as the populations
+  if (e == cudaSuccess) e = cudaMemset(h->d_flags, 0, N + STAGE_PAD_BYTES);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_nbmask, sizeof(uint32_t) * N);
   if (e == cudaSuccess) e = cudaMalloc(&raw, N);
   if (e == cudaSuccess) e = cudaMemcpy(raw, flags, N, cudaMemcpyHostToDevice);
@@ -372,9 +427,22 @@ int lbm_step(lbm_t h, int n) {
         e = h->fns[K_TWOPOP](a, h->threads, h->stream);
         h->cur ^= 1;
         break;
-      case LBM_AA:
-        e = h->fns[(h->steps & 1) ? K_AA_ODD : K_AA_EVEN](a, h->threads, h->stream);
+      case LBM_AA: {
+        const int odd = (int)(h->steps & 1);
+        if (h->sfns[odd]) {
+          rc = ensure_nonbulk_list(h);
+          if (rc) return rc;
+          Listed listed;
+          listed.cell = h->d_list;
+          listed.mask = h->d_list_mask;
+          listed.kinds = h->d_list_kinds;
+          listed.n = h->nlist;
+          e = h->sfns[odd](a, h->d_err, listed, h->stream);
+        } else {
+          e = h->fns[odd ? K_AA_ODD : K_AA_EVEN](a, h->threads, h->stream);
+        }
         break;
+      }
       case LBM_SWAP:
         e = h->fns[K_AA_EVEN](a, h->threads, h->stream);
         if (e == cudaSuccess) e = launch_swap_stream(h->Q, h->prec, h->layout, a, h->threads, h->stream);
@@ -428,6 +496,7 @@ int lbm_get_populations(lbm_t h, double* f) {
   if (!dev) {
     LBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return check_device_error(h);
   }
   return LBM_OK;
 }
@@ -462,6 +531,8 @@ int lbm_reduce(lbm_t h, double* mass, double* energy) {
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   if (mass) *mass = r[0];
   if (energy) *energy = r[1];
+  const int rc = check_device_error(h);
+  if (rc) return rc;
   if (!std::isfinite(r[0]) || !std::isfinite(r[1])) return fail(LBM_ERR_DIVERGED, "mass or energy is not finite");
   return LBM_OK;
 }
@@ -474,10 +545,11 @@ int lbm_steps_done(lbm_t h, long long* steps) {
 
 int lbm_device_bytes(lbm_t h, size_t* bytes) {
   if (!h || !bytes) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
-  size_t b = (size_t)h->N * (1 + sizeof(uint32_t)) + sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2) +
-             h->stage_bytes;
+  size_t b = (size_t)h->N * (1 + sizeof(uint32_t)) + STAGE_PAD_BYTES +
+             sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2) + h->stage_bytes + 2 * sizeof(int) +
+             (h->nlist > 0 ? (sizeof(int) + sizeof(uint32_t) + 2 * sizeof(unsigned long long)) * (size_t)h->nlist : 0);
   for (int a = 0; a < 2; ++a)
-    if (h->d_pop[a]) b += pop_bytes(h);
+    if (h->d_pop[a]) b += pop_bytes(h) + STAGE_PAD_BYTES;
   *bytes = b;
   return LBM_OK;
 }
@@ -488,6 +560,20 @@ int lbm_bytes_per_cell_update(lbm_t h, double* bytes) {
   // two-population, AA and esoteric twist read and write every population once;
   // swap reads and writes them twice (collision pass, then streaming pass)
   *bytes = h->scheme == LBM_SWAP ? 4.0 * pops + 2.0 : 2.0 * pops + 1.0;
+  return LBM_OK;
+}
+
+int lbm_kernels_per_step(lbm_t h, int* n) {
+  if (!h || !n) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  int k = 1;
+  if (h->scheme == LBM_SWAP) {
+    k = 2;
+  } else if (h->scheme == LBM_AA && h->sfns[0]) {
+    const int rc = ensure_nonbulk_list(h);
+    if (rc) return rc;
+    k = h->nlist > 0 ? 2 : 1;
+  }
+  *n = k;
   return LBM_OK;
 }
 
@@ -503,6 +589,11 @@ int lbm_destroy(lbm_t h) {
   if (h->d_wallu) cudaFree(h->d_wallu);
   if (h->d_partials) cudaFree(h->d_partials);
   if (h->d_stage) cudaFree(h->d_stage);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_list) cudaFree(h->d_list);
+  if (h->d_tile_off) cudaFree(h->d_tile_off);
+  if (h->d_list_mask) cudaFree(h->d_list_mask);
+  if (h->d_list_kinds) cudaFree(h->d_list_kinds);
   delete h;
   return LBM_OK;
 }

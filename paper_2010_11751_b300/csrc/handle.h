@@ -31,6 +31,14 @@ struct lbm_s {
   size_t stage_bytes = 0;
   int threads = 256;
   lbm::StepFn fns[lbm::NUM_STEP_KINDS] = {};
+  lbm::StagedFn sfns[2] = {};  // staged AA even / odd steps, or null (one-thread-per-cell kernels)
+  int* d_err = nullptr;        // [0] error word of the staged kernels, [1] scratch counter
+  // fluid cells with a non-zero flag byte (staged steps), sorted, and their records
+  int* d_list = nullptr;
+  uint32_t* d_list_mask = nullptr;
+  unsigned long long* d_list_kinds = nullptr;
+  int* d_tile_off = nullptr;   // per-tile offsets, only while the list is built
+  int nlist = -1;              // number of listed cells; -1 until the list is built
 };
 
 namespace lbm {

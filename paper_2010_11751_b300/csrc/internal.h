@@ -9,13 +9,34 @@ namespace lbm {
 
 struct KArgs;
 struct BatchArgs;
+
+// the staged AA kernels widen each bulk copy to 128-byte boundaries (whole L2
+// lines), so population and flag arrays carry this many bytes past their end
+constexpr int RUN_ALIGN_BYTES = 128;
+constexpr size_t STAGE_PAD_BYTES = RUN_ALIGN_BYTES;
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
 using BatchFn = cudaError_t (*)(const BatchArgs&, int sk, int blocks, int threads, cudaStream_t);
+// the fluid cells that are not bulk cells (flag byte non-zero), sorted, with a
+// record each: solid-neighbour mask | domain-face bit << 31, and the wall kind
+// of every solid neighbour (3 bits per link; links 0..20 in kinds[2t], 21..26
+// in kinds[2t + 1])
+struct Listed {
+  const int* cell = nullptr;
+  const uint32_t* mask = nullptr;
+  const unsigned long long* kinds = nullptr;
+  int n = 0;
+};
+// staged AA step: bulk cells through the shared-memory tile pipeline, listed
+// cells from their records; err receives the kernel's error word
+using StagedFn = cudaError_t (*)(const KArgs&, int* err, const Listed& listed, cudaStream_t);
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);
 // batched AA kernel (SoA) for (lattice, model, precision); nullptr if not built
 BatchFn batch_fn(int model, int Q, int P);
+// staged AA step (SoA) for (lattice, model, precision, K_AA_EVEN / K_AA_ODD);
+// nullptr where the one-thread-per-cell kernels are used
+StagedFn staged_fn(int model, int Q, int P, int SK);
 
 cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, uint32_t* mask, int nx, int ny, int nz,
                             cudaStream_t s);
@@ -29,6 +50,16 @@ int reduce_partials_count(int N);
 cudaError_t launch_reduce(int Q, int P, int L, int LD, const KArgs& a, double* partials, double* out2,
                           cudaStream_t s);
 cudaError_t launch_swap_stream(int Q, int P, int L, const KArgs& a, int threads, cudaStream_t s);
+// the fluid cells whose flag byte is non-zero, per tile of `tile` cells:
+// counts[t] = their number in tile t; then, from the exclusive prefix sums
+// offsets[t], their indices in ascending order into list
+cudaError_t launch_list_count(const uint8_t* flags, int N, int tile, int* counts, cudaStream_t s);
+cudaError_t launch_list_fill(const uint8_t* flags, int N, int tile, const int* offsets, int* list, cudaStream_t s);
+// the records of the n listed cells (see Listed)
+cudaError_t launch_listed_records(int Q, const KArgs& a, const int* list, int n, uint32_t* mask,
+                                  unsigned long long* kinds, cudaStream_t s);
+// cells per tile of the staged AA kernels of lattice Q
+constexpr int staged_tile(int Q) { return Q == 19 ? 1024 : 512; }
 
 // record the calling thread's last error text (read back by lbm_last_error) and return code
 int set_error(int code, const char* msg);

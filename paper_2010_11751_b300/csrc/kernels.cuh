@@ -103,6 +103,8 @@ struct Nb {
   bool edge;
   uint32_t mask;
   const uint8_t* flags;
+  // neighbourhood of cell i_ from its flag byte (the solid-neighbour mask is
+  // read from a.nbmask for cells next to a wall)
   __device__ __forceinline__ Nb(int i_, const KArgs& a, uint8_t fl = 0)
       : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
     sxy = a.ny * a.nz;
@@ -119,6 +121,21 @@ struct Nb {
         y = r / nz;
         z = r - y * nz;
       }
+    }
+  }
+  // neighbourhood of cell i_ from a given solid-neighbour mask and domain-face bit
+  __device__ __forceinline__ Nb(int i_, const KArgs& a, bool edge_, uint32_t mask_)
+      : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
+    static_assert(!FAST, "bulk cells have neither solid neighbours nor wrap");
+    sxy = a.ny * a.nz;
+    x = y = z = 0;
+    edge = edge_;
+    mask = mask_;
+    if (edge) {
+      x = i / sxy;
+      const int r = i - x * sxy;
+      y = r / nz;
+      z = r - y * nz;
     }
   }
   // index of the cell at offset (dx, dy, dz), periodic
@@ -152,6 +169,21 @@ struct Nb {
   }
 };
 
+// neighbourhood of a listed cell from its record (solid mask, domain-face bit
+// and the wall kind of every solid neighbour, 3 bits per link: links 0..20 in
+// kinds0, 21..26 in kinds1), so that no flag byte is read
+struct NbRec : Nb<false> {
+  unsigned long long kinds0, kinds1;
+  __device__ __forceinline__ NbRec(int i_, const KArgs& a, uint32_t mask_edge, unsigned long long k0,
+                                   unsigned long long k1)
+      : Nb<false>(i_, a, (mask_edge >> 31) != 0u, mask_edge & 0x7fffffffu), kinds0(k0), kinds1(k1) {}
+  template <int Q, int K>
+  __device__ __forceinline__ int kind() const {
+    if constexpr (K < 21) return (int)((kinds0 >> (3 * K)) & 7ull);
+    else return (int)((kinds1 >> (3 * (K - 21))) & 7ull);
+  }
+};
+
 template <int Q, int K>
 __host__ __device__ constexpr int cpos(int d) { return Lat<Q>::c(K, d) > 0 ? Lat<Q>::c(K, d) : 0; }
 template <int Q, int K>
@@ -166,8 +198,8 @@ __host__ __device__ constexpr int et_slot(bool bounced) {
 // ---------------------------------------------------------------------------
 // canonical load: the pre-collision populations of cell i, for the state kind
 // ---------------------------------------------------------------------------
-template <int Q, int P, int L, int LD, bool FAST, typename T>
-__device__ __forceinline__ void load_cell(const KArgs& a, const Nb<FAST>& nb, const void* pop, T (&f)[Q]) {
+template <int Q, int P, int L, int LD, bool FAST, typename T, class NB>
+__device__ __forceinline__ void load_cell(const KArgs& a, const NB& nb, const void* pop, T (&f)[Q]) {
   const int N = a.N;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -227,11 +259,10 @@ __device__ __forceinline__ void step_load(const KArgs& a, int i, typename Store<
   }
 }
 
-template <int Q, int P, int L, int SK, bool FAST>
-__device__ __forceinline__ void step_store(const KArgs& a, int i, const typename Store<P>::R (&f)[Q],
-                                           uint8_t fl = 0) {
+template <int Q, int P, int L, int SK, class NB>
+__device__ __forceinline__ void step_store_nb(const KArgs& a, const NB& nb, const typename Store<P>::R (&f)[Q]) {
   using R = typename Store<P>::R;
-  const Nb<FAST> nb(i, a, fl);
+  const int i = nb.i;
   const int N = a.N;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -258,6 +289,12 @@ __device__ __forceinline__ void step_store(const KArgs& a, int i, const typename
       }
     }
   });
+}
+
+template <int Q, int P, int L, int SK, bool FAST>
+__device__ __forceinline__ void step_store(const KArgs& a, int i, const typename Store<P>::R (&f)[Q],
+                                           uint8_t fl = 0) {
+  step_store_nb<Q, P, L, SK>(a, Nb<FAST>(i, a, fl), f);
 }
 
 // one cell update (load, collide, store); solid cells are left alone.

@@ -1,0 +1,303 @@
+// staged.cuh -- AA-pattern step kernels (SoA, FP32 / FP16 storage) whose
+// population reads are staged in shared memory by bulk asynchronous copies.
+//
+// A persistent block walks over tiles of TILE consecutive cells.  For each
+// tile one elected thread issues, per population label k, one bulk copy
+// (cp.async.bulk, completion counted on an mbarrier) of the contiguous run of
+// the source array that the tile's bulk cells read: for the even AA step the
+// cells' own slot k; for the odd step slot k-bar of the cells x - c_k, a run
+// shifted by the constant offset c_k . (ny nz, nz, 1).  With STAGES buffers in
+// flight per block, the bytes a multiprocessor has outstanding no longer
+// depend on how many loads its threads can hold in registers, which is what
+// limits the one-thread-per-cell kernels with 2-byte populations.
+//
+// The copies are whole 128-byte units (the run is widened to the enclosing
+// 128-byte boundaries), so the population and flag arrays carry 128 bytes of
+// padding past their end.  The staged kernel updates the bulk cells (flag
+// byte 0), reading their populations from shared memory.  The other fluid
+// cells (next to a wall or on a domain face: 1.2 % at 512^3) are updated
+// afterwards by a one-thread-per-cell kernel on the global-memory path, from a
+// sorted list with a record per cell built once per lattice (solid-neighbour
+// mask, domain-face bit, wall kinds of the solid neighbours), so that each
+// waits on two memory round trips (record, then populations) and reads no
+// flag byte.  Measured alternatives, all slower: the consumer warps taking
+// those cells inline, or extra warps taking them inside the stage pipeline
+// (their scattered global loads hold back the release of whole stages), or
+// extra warps working through them beside the pipeline (too few threads for
+// latency-bound work).  Stores go straight to global memory.  Every cell is
+// updated exactly as by the one-thread-per-cell kernels (same loads,
+// collision and stores; the cells of one AA step touch disjoint memory), so
+// the results are bit-identical to theirs.
+//
+// Warp roles: warp 0 is the producer (lane k issues the copy of label k, lane
+// Q the copy of the tile's flag bytes); warps 1..CW consume.  Each stage has
+// a `full` barrier (Q + 1 producer arrivals plus the copied bytes) and an
+// `empty` barrier (one arrival per consumer warp once it has read the stage),
+// so no block-wide barrier is taken inside the tile loop.
+//
+// Every wait on an mbarrier is bounded in time; on a timeout the thread
+// records an error code in *err and leaves the loop; the producer first waits
+// (bounded) for its own copies still in flight.
+#pragma once
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase with parity `phase` to complete; false after ~2 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, phase))
+    if (clock64() - t0 > (1LL << 32)) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// error codes written to *err by the staged kernels
+constexpr int STAGE_ERR_TIMEOUT = 1;
+
+
+template <int Q, int P, int TILE, int STAGES>
+struct StageLayout {
+  static constexpr int ES = (int)sizeof(typename Store<P>::S);  // bytes per stored population
+  static constexpr int ALIGN = RUN_ALIGN_BYTES / ES;             // elements per alignment unit
+  static_assert(TILE % 16 == 0, "TILE must be a multiple of 16 cells");
+  static_assert(Q + 1 <= 32, "one producer lane per label plus one for the flags");
+  static constexpr int SEG = TILE + 2 * ALIGN;  // elements per staged run
+  static constexpr int SEG_BYTES = SEG * ES;
+  static constexpr int STAGE_BYTES = Q * SEG_BYTES + TILE;  // runs, then the tile's flag bytes
+  // head: full[STAGES], empty[STAGES] barriers, then the run offsets [STAGES][Q]
+  static constexpr int HEAD = 128 * ((STAGES * 16 + STAGES * Q * 4 + 127) / 128);
+  static constexpr int BYTES = HEAD + STAGES * STAGE_BYTES;
+};
+
+// label k of the step kind reads population array `pop` at cell i - off
+template <int Q, int SK>
+__device__ __forceinline__ void stage_src(int k, int sxy, int nz, int& pop, int& off) {
+  pop = k;
+  off = 0;
+  if constexpr (SK == K_AA_ODD) {
+    static_for<0, Q>([&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      if (k == K && K != Lat<Q>::REST) {
+        pop = Lat<Q>::opp(K);
+        off = Lat<Q>::c(K, 0) * sxy + Lat<Q>::c(K, 1) * nz + Lat<Q>::c(K, 2);
+      }
+    });
+  }
+}
+
+// producer lane `lane` stages its part of tile `tile` into buffer `st`:
+// lanes 0..Q-1 one population run each, lane Q the flag bytes; every one of
+// these Q + 1 lanes arrives once on full[st]
+template <int Q, int P, int SK, int TILE, int STAGES>
+__device__ __forceinline__ void stage_issue_lane(const KArgs& a, unsigned char* smem, int tile, int st, int lane) {
+  using G = StageLayout<Q, P, TILE, STAGES>;
+  const uint32_t full = smem_addr(smem + 8 * st);
+  int* s_off = reinterpret_cast<int*>(smem + 16 * STAGES) + st * Q;
+  unsigned char* buf = smem + G::HEAD + st * G::STAGE_BYTES;
+  const long long N = a.N;
+  const long long base = (long long)tile * TILE;
+  const int cnt = (int)(N - base < TILE ? N - base : TILE);
+  if (lane < Q) {
+    int pk, off;
+    stage_src<Q, SK>(lane, a.ny * a.nz, a.nz, pk, off);
+    const long long p0 = (long long)pk * N;
+    const long long start = p0 + base - off;
+    // only bulk cells read the run, and their sources lie inside population pk
+    long long lo = start > p0 ? start : p0;
+    long long hi = start + cnt < p0 + N ? start + cnt : p0 + N;
+    if (hi > lo) {
+      lo &= ~(long long)(G::ALIGN - 1);
+      hi = (hi + G::ALIGN - 1) & ~(long long)(G::ALIGN - 1);
+      const uint32_t bytes = (uint32_t)((hi - lo) * G::ES);
+      s_off[lane] = (int)(start - lo);
+      mbar_arrive_expect_tx(full, bytes);
+      bulk_copy_g2s(smem_addr(buf + lane * G::SEG_BYTES),
+                    static_cast<const unsigned char*>(a.a) + lo * G::ES, bytes, full);
+    } else {
+      s_off[lane] = 0;  // no bulk cell of the tile reads this label
+      mbar_arrive(full);
+    }
+  } else if (lane == Q) {
+    const uint32_t fbytes = (uint32_t)((cnt + 15) & ~15);
+    mbar_arrive_expect_tx(full, fbytes);
+    bulk_copy_g2s(smem_addr(buf + Q * G::SEG_BYTES), a.flags + base, fbytes, full);
+  }
+}
+
+template <int Q, int M, int P>
+inline constexpr int STAGED_MIN_BLOCKS = (M == BGK_W2 || M == TRT || M == REG) ? 2 : 1;
+
+// one producer warp and CW consumer warps per block
+template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW>
+__global__ void __launch_bounds__(32 * (1 + CW), STAGED_MIN_BLOCKS<Q, M, P>)
+    staged_aa_kernel(KArgs a, int ntiles, int* err) {
+  using G = StageLayout<Q, P, TILE, STAGES>;
+  using R = typename Store<P>::R;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_addr(smem + 8 * s), Q + 1);             // full
+      mbar_init(smem_addr(smem + 8 * (STAGES + s)), CW);     // empty
+    }
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // producer
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int st = it % STAGES;
+      if (it >= STAGES) {
+        // wait until every consumer warp has released the previous use of st
+        const uint32_t ph = (uint32_t)((it / STAGES - 1) & 1);
+        if (!mbar_wait_bounded(smem_addr(smem + 8 * (STAGES + st)), ph)) {
+          if (lane == 0) {
+            atomicOr(err, STAGE_ERR_TIMEOUT);
+            // copies of the stages issued before this one may still be in flight
+            for (int j = it - STAGES + 1; j < it; ++j)
+              mbar_wait_bounded(smem_addr(smem + 8 * (j % STAGES)), (uint32_t)((j / STAGES) & 1));
+          }
+          return;
+        }
+      }
+      stage_issue_lane<Q, P, SK, TILE, STAGES>(a, smem, tile, st, lane);
+    }
+    return;
+  }
+  // consumers: the bulk cells of each tile, from the staged runs
+  const CP<R> cp = rates<P>(a);
+  const int ct = threadIdx.x - 32;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = it % STAGES;
+    const uint32_t full = smem_addr(smem + 8 * st);
+    if (!mbar_wait_bounded(full, (uint32_t)((it / STAGES) & 1))) {
+      if (lane == 0) atomicOr(err, STAGE_ERR_TIMEOUT);
+      return;
+    }
+    const int* s_off = reinterpret_cast<const int*>(smem + 16 * STAGES) + st * Q;
+    const unsigned char* buf = smem + G::HEAD + st * G::STAGE_BYTES;
+    const uint8_t* sflags = buf + Q * G::SEG_BYTES;
+    const int base = tile * TILE;
+    const int cnt = a.N - base < TILE ? a.N - base : TILE;
+    for (int c = ct; c < cnt; c += 32 * CW) {
+      if (sflags[c] != 0) continue;  // solid, or a listed cell
+      R f[Q];
+      static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const auto* run = reinterpret_cast<const typename Store<P>::S*>(buf + k * G::SEG_BYTES);
+        f[k] = Store<P>::to_r(run[s_off[k] + c]);
+      });
+      collide<Q, M, R, Store<P>::shifted>(f, cp);
+      step_store<Q, P, SOA, SK, true>(a, base + c, f);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_addr(smem + 8 * (STAGES + st)));  // release stage st
+  }
+}
+
+// the listed cells, one thread each, from their records
+template <int Q, int M, int P, int SK>
+__global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed listed) {
+  using R = typename Store<P>::R;
+  constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : LD_LOCAL;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= listed.n) return;
+  const NbRec nb(__ldg(listed.cell + t), a, __ldg(listed.mask + t), __ldg(listed.kinds + 2 * (size_t)t),
+                 __ldg(listed.kinds + 2 * (size_t)t + 1));
+  R f[Q];
+  load_cell<Q, P, SOA, LD, false>(a, nb, a.a, f);
+  const CP<R> cp = rates<P>(a);
+  collide<Q, M, R, Store<P>::shifted>(f, cp);
+  step_store_nb<Q, P, SOA, SK>(a, nb, f);
+}
+
+// tile shape per lattice: TILE cells, STAGES buffers, CW consumer warps
+template <int Q>
+struct StagedShape {
+  static constexpr int TILE = staged_tile(Q);
+  static constexpr int STAGES = 2;
+  static constexpr int CW = 8;
+};
+
+// one AA step (SK = K_AA_EVEN or K_AA_ODD) of the whole lattice: the staged
+// kernel over the bulk cells, then the listed-cell kernel
+template <int Q, int M, int P, int SK>
+cudaError_t launch_staged_step(const KArgs& a, int* err, const Listed& listed, cudaStream_t s) {
+  using Sh = StagedShape<Q>;
+  using G = StageLayout<Q, P, Sh::TILE, Sh::STAGES>;
+  constexpr int threads = 32 * (1 + Sh::CW);
+  auto kern = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW>;
+  // blocks of the persistent grid: resident blocks per SM x SMs (set once)
+  static const int grid = [&] {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) != cudaSuccess) return 0;
+    int occ = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, G::BYTES) != cudaSuccess) return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return (occ > 0 ? occ : 1) * sms;
+  }();
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  const int ntiles = (a.N + Sh::TILE - 1) / Sh::TILE;
+  if (ntiles > 0) kern<<<ntiles < grid ? ntiles : grid, threads, G::BYTES, s>>>(a, ntiles, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || listed.n <= 0) return e;
+  listed_cells_kernel<Q, M, P, SK><<<(listed.n + 127) / 128, 128, 0, s>>>(a, listed);
+  return cudaGetLastError();
+}
+
+// staged AA step of one model, for FP16 storage (SoA); nullptr elsewhere.
+// FP16 populations are where it pays: 2-byte loads leave the one-thread-per-cell
+// kernels short of bytes in flight.  FP32 and FP64 keep those kernels (FP32
+// already runs near the HBM roof, FP64 is bound by the FP64 pipe).
+template <int M>
+StagedFn staged_fn_for_model(int Q, int P, int SK) {
+  if (P != F16) return nullptr;
+  if (Q == 19) return SK == K_AA_EVEN ? &launch_staged_step<19, M, F16, K_AA_EVEN>
+                                      : (SK == K_AA_ODD ? &launch_staged_step<19, M, F16, K_AA_ODD> : nullptr);
+  if (Q == 27) return SK == K_AA_EVEN ? &launch_staged_step<27, M, F16, K_AA_EVEN>
+                                      : (SK == K_AA_ODD ? &launch_staged_step<27, M, F16, K_AA_ODD> : nullptr);
+  return nullptr;
+}
+
+}  // namespace lbm

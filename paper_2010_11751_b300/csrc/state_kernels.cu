@@ -370,4 +370,80 @@ cudaError_t launch_swap_stream(int Q, int P, int L, const KArgs& a, int threads,
   });
 }
 
+// ---------------------------------------------------------------------------
+// list of the fluid cells that are not bulk cells (flag byte non-zero and not
+// solid), sorted, with the offset of every tile of `tile` cells into it: one
+// warp per tile counts (pass 1), then writes its cells in order (pass 2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool nonbulk_fluid(uint8_t f) { return f != 0 && (f & FLAG_KIND) == 0; }
+
+__global__ void tile_count_kernel(const uint8_t* flags, int N, int tile, int ntiles, int* counts) {
+  const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (t >= ntiles) return;
+  const long long b = (long long)t * tile, e = b + tile < N ? b + tile : N;
+  int c = 0;
+  for (long long i = b + lane; i < e; i += 32) c += nonbulk_fluid(flags[i]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) counts[t] = c;
+}
+
+__global__ void tile_fill_kernel(const uint8_t* flags, int N, int tile, int ntiles, const int* offsets, int* list) {
+  const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (t >= ntiles) return;
+  const long long b = (long long)t * tile, e = b + tile < N ? b + tile : N;
+  int at = offsets[t];
+  for (long long i0 = b; i0 < e; i0 += 32) {
+    const long long i = i0 + lane;
+    const bool pred = i < e && nonbulk_fluid(flags[i]);
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (pred) list[at + __popc(m & ((1u << lane) - 1u))] = (int)i;
+    at += __popc(m);
+  }
+}
+
+cudaError_t launch_list_count(const uint8_t* flags, int N, int tile, int* counts, cudaStream_t s) {
+  const int ntiles = (N + tile - 1) / tile;
+  const long long threads = 32LL * ntiles;
+  if (ntiles > 0) tile_count_kernel<<<(int)((threads + 255) / 256), 256, 0, s>>>(flags, N, tile, ntiles, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_fill(const uint8_t* flags, int N, int tile, const int* offsets, int* list, cudaStream_t s) {
+  const int ntiles = (N + tile - 1) / tile;
+  const long long threads = 32LL * ntiles;
+  if (ntiles > 0) tile_fill_kernel<<<(int)((threads + 255) / 256), 256, 0, s>>>(flags, N, tile, ntiles, offsets, list);
+  return cudaGetLastError();
+}
+
+template <int Q>
+__global__ void listed_records_kernel(KArgs a, const int* list, int n, uint32_t* mask, unsigned long long* kinds) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = list[t];
+  const Nb<false> nb(i, a, a.flags[i]);
+  unsigned long long k0 = 0ull, k1 = 0ull;
+  static_for<0, Q>([&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    if constexpr (K != Lat<Q>::REST) {
+      if (nb.template solid<Q, K>()) {
+        const unsigned long long v = (unsigned long long)nb.template kind<Q, K>();
+        if constexpr (K < 21) k0 |= v << (3 * K);
+        else k1 |= v << (3 * (K - 21));
+      }
+    }
+  });
+  mask[t] = nb.mask | (nb.edge ? 0x80000000u : 0u);
+  kinds[2 * (size_t)t] = k0;
+  kinds[2 * (size_t)t + 1] = k1;
+}
+
+cudaError_t launch_listed_records(int Q, const KArgs& a, const int* list, int n, uint32_t* mask,
+                                  unsigned long long* kinds, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int b = (n + 255) / 256;
+  if (Q == 19) listed_records_kernel<19><<<b, 256, 0, s>>>(a, list, n, mask, kinds);
+  else listed_records_kernel<27><<<b, 256, 0, s>>>(a, list, n, mask, kinds);
+  return cudaGetLastError();
+}
+
 }  // namespace lbm

@@ -26,6 +26,17 @@ BatchFn batch_fn_cm(int, int);
 BatchFn batch_fn_chm(int, int);
 BatchFn batch_fn_k(int, int);
 
+StagedFn staged_fn_bgk_w2(int, int, int);
+StagedFn staged_fn_bgk_nw4(int, int, int);
+StagedFn staged_fn_trt(int, int, int);
+StagedFn staged_fn_reg(int, int, int);
+StagedFn staged_fn_rr(int, int, int);
+StagedFn staged_fn_rm(int, int, int);
+StagedFn staged_fn_hm(int, int, int);
+StagedFn staged_fn_cm(int, int, int);
+StagedFn staged_fn_chm(int, int, int);
+StagedFn staged_fn_k(int, int, int);
+
 StepFn step_fn(int model, int Q, int P, int L, int SK) {
   switch (model) {
     case BGK_W2: return step_fn_bgk_w2(Q, P, L, SK);
@@ -53,6 +64,21 @@ BatchFn batch_fn(int model, int Q, int P) {
     case CM: return batch_fn_cm(Q, P);
     case CHM: return batch_fn_chm(Q, P);
     case KUM: return batch_fn_k(Q, P);
+    default: return nullptr;
+  }
+}
+StagedFn staged_fn(int model, int Q, int P, int SK) {
+  switch (model) {
+    case BGK_W2: return staged_fn_bgk_w2(Q, P, SK);
+    case BGK_NW4: return staged_fn_bgk_nw4(Q, P, SK);
+    case TRT: return staged_fn_trt(Q, P, SK);
+    case REG: return staged_fn_reg(Q, P, SK);
+    case RR: return staged_fn_rr(Q, P, SK);
+    case RM: return staged_fn_rm(Q, P, SK);
+    case HM: return staged_fn_hm(Q, P, SK);
+    case CM: return staged_fn_cm(Q, P, SK);
+    case CHM: return staged_fn_chm(Q, P, SK);
+    case KUM: return staged_fn_k(Q, P, SK);
     default: return nullptr;
   }
 }

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
         "lbm_steps_done": [vp, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_device_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
         "lbm_bytes_per_cell_update": [vp, ctypes.POINTER(d)],
+        "lbm_kernels_per_step": [vp, ctypes.POINTER(i)],
         "lbm_destroy": [vp],
         "lbm_supported": [i, i, i, i, i],
         "lbm_conserved_sums_static": [i, i, dp, u8p, dp, vp],
@@ -181,6 +182,12 @@ def lbm_device_bytes(h):
 def lbm_bytes_per_cell_update(h):
     v = ctypes.c_double()
     _check(lib().lbm_bytes_per_cell_update(h, ctypes.byref(v)))
+    return v.value
+
+
+def lbm_kernels_per_step(h):
+    v = ctypes.c_int()
+    _check(lib().lbm_kernels_per_step(h, ctypes.byref(v)))
     return v.value
 
 
