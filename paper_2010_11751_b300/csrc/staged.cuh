@@ -20,11 +20,13 @@
 // sorted list with a record per cell built once per lattice (solid-neighbour
 // mask, domain-face bit, wall kinds of the solid neighbours), so that each
 // waits on two memory round trips (record, then populations) and reads no
-// flag byte.  Measured alternatives, all slower: the consumer warps taking
-// those cells inline, or extra warps taking them inside the stage pipeline
-// (their scattered global loads hold back the release of whole stages), or
-// extra warps working through them beside the pipeline (too few threads for
-// latency-bound work).  Stores go straight to global memory.  Every cell is
+// flag byte.  Updating those cells while the bulk copies stream was measured
+// 1.5 to 5 times slower in every form tried (inline in the consumer loop, by
+// extra warps inside the stage pipeline, or by extra warps beside it, paced
+// to the tile being staged or not): their scattered loads queue behind the
+// bulk copies that keep HBM busy, taking ~18 us for a tile's dozen cells, and
+// inside the pipeline they hold back the release of whole stages.  Stores go
+// straight to global memory.  Every cell is
 // updated exactly as by the one-thread-per-cell kernels (same loads,
 // collision and stores; the cells of one AA step touch disjoint memory), so
 // the results are bit-identical to theirs.
