@@ -138,7 +138,11 @@ LBM_API int lbm_init_equilibrium(lbm_t h, const double* rho, const double* u);
 
 /* Enqueue n >= 0 time iterations on the handle's stream; asynchronous.  If
  * the populations were never written, they are first set to the equilibrium
- * at rho = 1, u = 0. */
+ * at rho = 1, u = 0.  The first AA step of an FP16 SoA handle also builds
+ * (once, synchronously) the list of cells next to a wall or on a domain face
+ * that its staged steps update separately.  The staged steps wait on their
+ * shared-memory copies with a ~2 s bound; a wait that gives up is reported by
+ * the next lbm_reduce or host lbm_get_populations as LBM_ERR_TIMEOUT. */
 LBM_API int lbm_step(lbm_t h, int n);
 
 /* rho[N] and u[3*N] (FP64) of the current pre-collision state; host or device.
@@ -146,7 +150,9 @@ LBM_API int lbm_step(lbm_t h, int n);
 LBM_API int lbm_macroscopic(lbm_t h, double* rho, double* u);
 
 /* Canonical populations f[Q*N] (FP64, [Q][N]); host or device.  Shifted
- * storage is un-shifted (f = stored + t_k).  Solid cells read 0. */
+ * storage is un-shifted (f = stored + t_k).  Solid cells read 0.  With a host
+ * buffer: synchronises the stream and returns LBM_ERR_TIMEOUT if a staged
+ * step gave up waiting (see lbm_step). */
 LBM_API int lbm_get_populations(lbm_t h, double* f);
 
 /* Load canonical populations f[Q*N]; host or device.  Solid-cell entries are
@@ -154,7 +160,8 @@ LBM_API int lbm_get_populations(lbm_t h, double* f);
 LBM_API int lbm_set_populations(lbm_t h, const double* f);
 
 /* FP64 sums over fluid cells: mass = sum rho, energy = sum rho |u|^2 / 2.
- * Host outputs; synchronises the stream.  LBM_ERR_DIVERGED if either is not
+ * Host outputs; synchronises the stream.  LBM_ERR_TIMEOUT if a staged step
+ * gave up waiting (see lbm_step); else LBM_ERR_DIVERGED if either sum is not
  * finite (the outputs are still written). */
 LBM_API int lbm_reduce(lbm_t h, double* mass, double* energy);
 

@@ -1,8 +1,8 @@
-// staged.cuh -- AA-pattern step kernels (SoA, FP32 / FP16 storage) whose
-// population reads are staged in shared memory by bulk asynchronous copies.
+// staged.cuh -- AA-pattern step of FP16-stored populations (SoA) whose reads
+// are staged in shared memory by bulk asynchronous copies.
 //
 // A persistent block walks over tiles of TILE consecutive cells.  For each
-// tile one elected thread issues, per population label k, one bulk copy
+// tile a producer warp issues, per population label k, one bulk copy
 // (cp.async.bulk, completion counted on an mbarrier) of the contiguous run of
 // the source array that the tile's bulk cells read: for the even AA step the
 // cells' own slot k; for the odd step slot k-bar of the cells x - c_k, a run
@@ -26,10 +26,10 @@
 // to the tile being staged or not): their scattered loads queue behind the
 // bulk copies that keep HBM busy, taking ~18 us for a tile's dozen cells, and
 // inside the pipeline they hold back the release of whole stages.  Stores go
-// straight to global memory.  Every cell is
-// updated exactly as by the one-thread-per-cell kernels (same loads,
-// collision and stores; the cells of one AA step touch disjoint memory), so
-// the results are bit-identical to theirs.
+// straight to global memory.  Every cell is updated exactly as by the
+// one-thread-per-cell kernels (same loads, collision and stores; the cells of
+// one AA step touch disjoint memory), so the results are bit-identical to
+// theirs.
 //
 // Warp roles: warp 0 is the producer (lane k issues the copy of label k, lane
 // Q the copy of the tile's flag bytes); warps 1..CW consume.  Each stage has
@@ -51,12 +51,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_inval(uint32_t bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
