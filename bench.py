@@ -51,7 +51,7 @@ FP64_OPS_PER_CLK = 296
 KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh"]
 TRAFFIC = {
     # (precision, lattice, collision, scheme, n): (bytes per AA-odd launch, source hash)
-    ("f64", 19, "BGK_W2", "aa", 256): (2544815360 + 2448811264, "46b10fc809b204bf"),
+    ("f64", 19, "BGK_W2", "aa", 256): (2545243648 + 2449016064, "e9c29894a8a4b03c"),
 }
 
 
