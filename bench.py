@@ -247,7 +247,8 @@ def time_native(args, rank, local, pg):
 
 def e2e_native(args, L, torch):
     """Same metric through the public C ABI with host buffers: host (rho, u) -> init, K x
-    (step + FP64 conserved sums read back), host (rho, u) read back at the end."""
+    lbm_step_sums(1) (one step and the FP64 conserved sums of the state it read, read back to
+    the host), host (rho, u) read back at the end."""
     n, omega, flags, walls = workload(args)
     N = n ** 3
     rho = torch.ones(N, dtype=torch.float64).pin_memory()
@@ -263,15 +264,15 @@ def e2e_native(args, L, torch):
     t0 = time.perf_counter()
     g.init_equilibrium(rho, u)
     for _ in range(args.steps):
-        g.step(1)
-        g.reduce()
+        g.step_sums(1)  # one step, and the FP64 mass and energy of the state it read, to the host
     g.macroscopic(rho_out, u_out)
     t1 = time.perf_counter()
     g.close()
     mlups = N * args.steps / (t1 - t0) / 1e6
     return {"value": round(mlups, 2), "unit": "MLUPS", "h2d_bytes_per_step": int(32 * N / args.steps),
             "d2h_bytes_per_step": int(16 + 32 * N / args.steps),
-            "note": "host rho/u upload, K x (step + FP64 mass/energy read back), host rho/u download"}
+            "note": "host rho/u upload, K x lbm_step_sums(1) (step + FP64 mass/energy of the state it read, "
+                    "read back), host rho/u download"}
 
 
 def oracle_baseline(args, seconds, max_steps=None, warmup=0):

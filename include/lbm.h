@@ -145,6 +145,16 @@ LBM_API int lbm_init_equilibrium(lbm_t h, const double* rho, const double* u);
  * the next lbm_reduce or host lbm_get_populations as LBM_ERR_TIMEOUT. */
 LBM_API int lbm_step(lbm_t h, int n);
 
+/* lbm_reduce followed by lbm_step(h, n), in fewer passes over memory: the
+ * FP64 mass and energy (as lbm_reduce defines them) of the state the call
+ * starts from, computed by the first of the n steps from the moments its
+ * collision forms anyway (for n = 0 it is lbm_reduce).  Handles without such a
+ * kernel (AoS layout, the staged FP16 AA steps) run the reduction, then the
+ * steps.  The sums agree with lbm_reduce's up to FP64 summation order; FP32
+ * and FP16 storage form each cell's share in FP32.  Synchronises the stream;
+ * errors as lbm_reduce. */
+LBM_API int lbm_step_sums(lbm_t h, int n, double* mass, double* energy);
+
 /* rho[N] and u[3*N] (FP64) of the current pre-collision state; host or device.
  * Either may be NULL.  Synchronises the handle's stream for host outputs. */
 LBM_API int lbm_macroscopic(lbm_t h, double* rho, double* u);

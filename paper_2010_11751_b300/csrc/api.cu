@@ -76,6 +76,7 @@ int resolve_kernels(lbm_s* h) {
   const bool staged = h->scheme == LBM_AA && h->layout == SOA;
   h->sfns[0] = staged ? staged_fn(h->model, h->Q, h->prec, K_AA_EVEN) : nullptr;
   h->sfns[1] = staged ? staged_fn(h->model, h->Q, h->prec, K_AA_ODD) : nullptr;
+  for (int sk = 0; sk < NUM_STEP_KINDS; ++sk) h->sumfns[sk] = step_sum_fn(h->model, h->Q, h->prec, h->layout, sk);
   return LBM_OK;
 }
 
@@ -410,6 +411,65 @@ int lbm_init_equilibrium(lbm_t h, const double* rho, const double* u) {
   return init_eq_device(h, dr, du);
 }
 
+namespace {
+// enqueue one time step; with sum_partials, the step's kernel also writes the
+// per-block FP64 sums of the state it reads (returns the number of blocks in
+// *nparts), and the caller guarantees that a summing kernel exists
+int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr) {
+  KArgs a = make_args(h);
+  cudaError_t e = cudaSuccess;
+  auto kernel = [&](int sk) {
+    if (sum_partials) {
+      *nparts = (h->N + h->threads - 1) / h->threads;
+      return h->sumfns[sk](a, h->threads, sum_partials, h->stream);
+    }
+    return h->fns[sk](a, h->threads, h->stream);
+  };
+  switch (h->scheme) {
+    case LBM_TWOPOP:
+      e = kernel(K_TWOPOP);
+      h->cur ^= 1;
+      break;
+    case LBM_AA: {
+      const int odd = (int)(h->steps & 1);
+      if (h->sfns[odd] && !sum_partials) {
+        const int rc = ensure_nonbulk_list(h);
+        if (rc) return rc;
+        Listed listed;
+        listed.cell = h->d_list;
+        listed.mask = h->d_list_mask;
+        listed.kinds = h->d_list_kinds;
+        listed.n = h->nlist;
+        e = h->sfns[odd](a, h->d_err, listed, h->stream);
+      } else {
+        e = kernel(odd ? K_AA_ODD : K_AA_EVEN);
+      }
+      break;
+    }
+    case LBM_SWAP:
+      e = kernel(K_AA_EVEN);
+      if (e == cudaSuccess) e = launch_swap_stream(h->Q, h->prec, h->layout, a, h->threads, h->stream);
+      break;
+    case LBM_ESOTWIST:
+      e = kernel(K_ESOTWIST);
+      break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+  ++h->steps;
+  return LBM_OK;
+}
+
+// step kind of the handle's next step
+int next_step_kind(const lbm_s* h) {
+  switch (h->scheme) {
+    case LBM_TWOPOP: return K_TWOPOP;
+    case LBM_AA: return (h->steps & 1) ? K_AA_ODD : K_AA_EVEN;
+    case LBM_SWAP: return K_AA_EVEN;
+    default: return K_ESOTWIST;
+  }
+}
+}  // namespace
+
 int lbm_step(lbm_t h, int n) {
   if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
   if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
@@ -420,40 +480,59 @@ int lbm_step(lbm_t h, int n) {
   int rc = upload_wall(h);
   if (rc) return rc;
   for (int s = 0; s < n; ++s) {
-    KArgs a = make_args(h);
-    cudaError_t e = cudaSuccess;
-    switch (h->scheme) {
-      case LBM_TWOPOP:
-        e = h->fns[K_TWOPOP](a, h->threads, h->stream);
-        h->cur ^= 1;
-        break;
-      case LBM_AA: {
-        const int odd = (int)(h->steps & 1);
-        if (h->sfns[odd]) {
-          rc = ensure_nonbulk_list(h);
-          if (rc) return rc;
-          Listed listed;
-          listed.cell = h->d_list;
-          listed.mask = h->d_list_mask;
-          listed.kinds = h->d_list_kinds;
-          listed.n = h->nlist;
-          e = h->sfns[odd](a, h->d_err, listed, h->stream);
-        } else {
-          e = h->fns[odd ? K_AA_ODD : K_AA_EVEN](a, h->threads, h->stream);
-        }
-        break;
-      }
-      case LBM_SWAP:
-        e = h->fns[K_AA_EVEN](a, h->threads, h->stream);
-        if (e == cudaSuccess) e = launch_swap_stream(h->Q, h->prec, h->layout, a, h->threads, h->stream);
-        break;
-      case LBM_ESOTWIST:
-        e = h->fns[K_ESOTWIST](a, h->threads, h->stream);
-        break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-    ++h->steps;
+    rc = enqueue_step(h);
+    if (rc) return rc;
   }
+  return LBM_OK;
+}
+
+int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return lbm_reduce(h, mass, energy);
+  if (!h->populated) {
+    int rc = init_eq_device(h, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  int rc = upload_wall(h);
+  if (rc) return rc;
+  double* out2 = h->d_partials + 2 * h->partials;
+  const int sk = next_step_kind(h);
+  const bool staged = h->scheme == LBM_AA && h->sfns[(int)(h->steps & 1)];
+  if (staged || !h->sumfns[sk]) {
+    // no summing kernel for this configuration: the reduction kernel reads the
+    // state first, then the steps run
+    KArgs a = make_args(h);
+    LBM_CUDA(launch_reduce(h->Q, h->prec, h->layout, load_kind(h), a, h->d_partials, out2, h->stream));
+    rc = lbm_step(h, n);
+    if (rc) return rc;
+  } else {
+    const size_t need = 2 * (size_t)((h->N + h->threads - 1) / h->threads);
+    if (h->sum_partials_cap < need) {
+      if (h->d_sum_partials) {
+        LBM_CUDA(cudaStreamSynchronize(h->stream));
+        LBM_CUDA(cudaFree(h->d_sum_partials));
+        h->d_sum_partials = nullptr;
+        h->sum_partials_cap = 0;
+      }
+      LBM_CUDA(cudaMalloc(&h->d_sum_partials, sizeof(double) * need));
+      h->sum_partials_cap = need;
+    }
+    int nparts = 0;
+    rc = enqueue_step(h, h->d_sum_partials, &nparts);
+    if (rc) return rc;
+    LBM_CUDA(launch_reduce_final(h->d_sum_partials, nparts, out2, h->stream));
+    rc = lbm_step(h, n - 1);
+    if (rc) return rc;
+  }
+  double r[2];
+  LBM_CUDA(cudaMemcpyAsync(r, out2, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (mass) *mass = r[0];
+  if (energy) *energy = r[1];
+  rc = check_device_error(h);
+  if (rc) return rc;
+  if (!std::isfinite(r[0]) || !std::isfinite(r[1])) return fail(LBM_ERR_DIVERGED, "mass or energy is not finite");
   return LBM_OK;
 }
 
@@ -546,7 +625,8 @@ int lbm_steps_done(lbm_t h, long long* steps) {
 int lbm_device_bytes(lbm_t h, size_t* bytes) {
   if (!h || !bytes) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
   size_t b = (size_t)h->N * (1 + sizeof(uint32_t)) + STAGE_PAD_BYTES +
-             sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2) + h->stage_bytes + 2 * sizeof(int) +
+             sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2 + h->sum_partials_cap) + h->stage_bytes +
+             2 * sizeof(int) +
              (h->nlist > 0 ? (sizeof(int) + sizeof(uint32_t) + 2 * sizeof(unsigned long long)) * (size_t)h->nlist : 0);
   for (int a = 0; a < 2; ++a)
     if (h->d_pop[a]) b += pop_bytes(h) + STAGE_PAD_BYTES;
@@ -590,6 +670,7 @@ int lbm_destroy(lbm_t h) {
   if (h->d_partials) cudaFree(h->d_partials);
   if (h->d_stage) cudaFree(h->d_stage);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->d_sum_partials) cudaFree(h->d_sum_partials);
   if (h->d_list) cudaFree(h->d_list);
   if (h->d_tile_off) cudaFree(h->d_tile_off);
   if (h->d_list_mask) cudaFree(h->d_list_mask);

@@ -41,6 +41,25 @@ struct CP {
 template <int Q, int K>
 inline constexpr int WCLASS = Lat<Q>::norm2(K);
 
+// one cell's share of the conserved sums (mass rho, kinetic energy rho |u|^2 / 2),
+// taken from the moments a collision computes anyway; accumulated in FP64
+struct CellSums {
+  double rho, ke;
+};
+// drho = rho - 1 for shifted storage (kept apart so that FP32 keeps its digits), rho otherwise
+template <typename R, bool SH>
+__device__ __forceinline__ void cell_sums(CellSums* cs, R drho, R ux, R uy, R uz) {
+  if (cs) {
+    // in FP64 with rounded intrinsics: no product here is shared with, or fused
+    // into, the collision's own arithmetic
+    const double rho = SH ? __dadd_rn(1.0, (double)drho) : (double)drho;
+    const double x = (double)ux, y = (double)uy, z = (double)uz;
+    const double u2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+    cs->rho = rho;
+    cs->ke = __dmul_rn(__dmul_rn(0.5, rho), u2);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
@@ -358,7 +377,7 @@ __device__ __forceinline__ Macro<Q, R, SH> macro_from_pairs(const R (&s)[Lat<Q>:
 // A = rho (1 - 1.5 u^2)  (shifted: A = drho - 1.5 rho u^2, giving E - t)
 // ---------------------------------------------------------------------------
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   constexpr int H = Lat<Q>::H;
   R s[H], d[H];
   pair_sums<Q>(f, s, d);
@@ -382,7 +401,12 @@ __device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p) {
     // single-lattice or batched, rounds identically)
     const R inv15 = R(1.5) / rho;
     const R vx = jx * inv15, vy = jy * inv15, vz = jz * inv15;
-    const R A = r - fma(vx, jx, fma(vy, jy, __dmul_rn(vz, jz)));  // rho (1 - 1.5 |u|^2) (shifted: minus 1)
+    const R vj = fma(vx, jx, fma(vy, jy, __dmul_rn(vz, jz)));  // 1.5 |j|^2 / rho
+    const R A = r - vj;  // rho (1 - 1.5 |u|^2) (shifted: minus 1)
+    if (cs) {
+      cs->rho = SH ? __dadd_rn(1.0, (double)r) : (double)r;
+      cs->ke = __dmul_rn((double)vj, 1.0 / 3.0);
+    }
     f[H] = fma(p.omc, f[H], __dmul_rn(p.wt[0], A));
     static_for<0, H>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -408,6 +432,10 @@ __device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p) {
     // A = rho (1 - 1.5 |u|^2) = rho - 1.5 u.j  (shifted: A - 1 = drho - 1.5 u.j)
     const R uj = ux * jx + uy * jy + uz * jz;
     const R A = r - R(1.5) * uj;
+    if (cs) {
+      cs->rho = SH ? __dadd_rn(1.0, (double)r) : (double)r;
+      cs->ke = __dmul_rn(0.5, (double)uj);
+    }
     f[H] = f[H] + p.omega * (R(WGT<Q, H>) * A - f[H]);
     static_for<0, H>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -433,7 +461,7 @@ __device__ __forceinline__ void collide_bgk_w2(R (&f)[Q], const CP<R>& p) {
 // Per opposite pair (plus member along e_k): E+ = t (A + 4.5 (e.u)(e.j)),
 // E-_plus = 3 t e.j, with j = rho u and A = rho (1 - 1.5 |u|^2).
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   constexpr int H = Lat<Q>::H;
   R s[H], d[H];
   pair_sums<Q>(f, s, d);
@@ -455,7 +483,12 @@ __device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p) {
     // (explicit fma / rounded adds, as in BGK-W2)
     const R inv15 = R(1.5) / rho;
     const R vx = jx * inv15, vy = jy * inv15, vz = jz * inv15;
-    const R A = r - fma(vx, jx, fma(vy, jy, __dmul_rn(vz, jz)));
+    const R vj = fma(vx, jx, fma(vy, jy, __dmul_rn(vz, jz)));  // 1.5 |j|^2 / rho
+    const R A = r - vj;
+    if (cs) {
+      cs->rho = SH ? __dadd_rn(1.0, (double)r) : (double)r;
+      cs->ke = __dmul_rn((double)vj, 1.0 / 3.0);
+    }
     f[H] = fma(p.omc, f[H], __dmul_rn(p.wt[0], A));
     static_for<0, H>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -479,6 +512,10 @@ __device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p) {
     const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
     const R uj = ux * jx + uy * jy + uz * jz;
     const R A = r - R(1.5) * uj;
+    if (cs) {
+      cs->rho = SH ? __dadd_rn(1.0, (double)r) : (double)r;
+      cs->ke = __dmul_rn(0.5, (double)uj);
+    }
     f[H] = f[H] - p.omega * (f[H] - R(WGT<Q, H>) * A);
     const R hp = R(0.5) * p.omega, hm = R(0.5) * p.trt_minus;
     static_for<0, H>([&](auto kc) {
@@ -503,11 +540,12 @@ __device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p) {
 // Regularized: f_out = E + (1 - w) t_k/(2 cs^4) H2_k : Pi_neq,
 // Pi_neq = sum_k c c (f - E); W2 equilibrium.
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_reg(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_reg(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   constexpr int H = Lat<Q>::H;
   R s[H], d[H];
   pair_sums<Q>(f, s, d);
   const auto m = macro_from_pairs<Q, R, SH>(s, d, f[H]);
+  cell_sums<R, SH>(cs, m.drho, m.ux, m.uy, m.uz);
   R pxx = R(-0.0), pyy = R(-0.0), pzz = R(-0.0), pxy = R(-0.0), pxz = R(-0.0), pyz = R(-0.0);
   static_for<0, H>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -645,9 +683,10 @@ __device__ __forceinline__ R uprod(R ux, R uy, R uz) {
 }
 
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_nw4(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_nw4(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   R E[Q], feq[Q];
   eq_raw<Q>(st.ux, st.uy, st.uz, E);
   store_moments<Q, R, SH>(E, st, feq);
@@ -658,24 +697,26 @@ __device__ __forceinline__ void collide_nw4(R (&f)[Q], const CP<R>& p) {
 }
 
 template <int Q, typename R, bool SH, bool HEQ>
-__device__ __forceinline__ void collide_rm_impl(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_rm_impl(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   R E[Q];
   eq_raw<Q>(st.ux, st.uy, st.uz, E);
   relax<Q, R, HEQ>(st.Mh, E, p);
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_rm(R (&f)[Q], const CP<R>& p) {
-  if (p.omega_high == R(1)) collide_rm_impl<Q, R, SH, true>(f, p);
-  else collide_rm_impl<Q, R, SH, false>(f, p);
+__device__ __forceinline__ void collide_rm(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if (p.omega_high == R(1)) collide_rm_impl<Q, R, SH, true>(f, p, cs);
+  else collide_rm_impl<Q, R, SH, false>(f, p, cs);
 }
 
 template <int Q, typename R, bool SH, bool HEQ>
-__device__ __forceinline__ void collide_hm_impl(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_hm_impl(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   all_axes<Q, 2, R, HEQ ? 2 : 6>(st.Mh, st.ux, st.uy, st.uz);  // monomial -> Hermite
   R E[Q];
   static_for<0, Q>([&](auto jc) {
@@ -687,9 +728,9 @@ __device__ __forceinline__ void collide_hm_impl(R (&f)[Q], const CP<R>& p) {
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_hm(R (&f)[Q], const CP<R>& p) {
-  if (p.omega_high == R(1)) collide_hm_impl<Q, R, SH, true>(f, p);
-  else collide_hm_impl<Q, R, SH, false>(f, p);
+__device__ __forceinline__ void collide_hm(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if (p.omega_high == R(1)) collide_hm_impl<Q, R, SH, true>(f, p, cs);
+  else collide_hm_impl<Q, R, SH, false>(f, p, cs);
 }
 
 // central-moment equilibrium prod k_p, k = (1, 0, cs2)
@@ -703,9 +744,10 @@ __device__ __forceinline__ void eq_central(R (&E)[Q]) {
 }
 
 template <int Q, typename R, bool SH, bool HEQ>
-__device__ __forceinline__ void collide_cm_impl(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_cm_impl(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
   all_axes<Q, 0, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // raw -> central
   R E[Q];
@@ -718,15 +760,16 @@ __device__ __forceinline__ void collide_cm_impl(R (&f)[Q], const CP<R>& p) {
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_cm(R (&f)[Q], const CP<R>& p) {
-  if (p.omega_high == R(1)) collide_cm_impl<Q, R, SH, true>(f, p);
-  else collide_cm_impl<Q, R, SH, false>(f, p);
+__device__ __forceinline__ void collide_cm(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if (p.omega_high == R(1)) collide_cm_impl<Q, R, SH, true>(f, p, cs);
+  else collide_cm_impl<Q, R, SH, false>(f, p, cs);
 }
 
 template <int Q, typename R, bool SH, bool HEQ>
-__device__ __forceinline__ void collide_chm_impl(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_chm_impl(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
   all_axes<Q, 0, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // raw -> central
   all_axes<Q, 2, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // central monomial -> central Hermite
@@ -744,9 +787,9 @@ __device__ __forceinline__ void collide_chm_impl(R (&f)[Q], const CP<R>& p) {
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_chm(R (&f)[Q], const CP<R>& p) {
-  if (p.omega_high == R(1)) collide_chm_impl<Q, R, SH, true>(f, p);
-  else collide_chm_impl<Q, R, SH, false>(f, p);
+__device__ __forceinline__ void collide_chm(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if (p.omega_high == R(1)) collide_chm_impl<Q, R, SH, true>(f, p, cs);
+  else collide_chm_impl<Q, R, SH, false>(f, p, cs);
 }
 
 // cumulants of orders 4..6 from normalised central moments (lower orders
@@ -792,9 +835,10 @@ __device__ __forceinline__ void cumulant_high(R (&X)[Q]) {
 }
 
 template <int Q, typename R, bool SH, bool HEQ>
-__device__ __forceinline__ void collide_k_impl(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_k_impl(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH, HEQ ? 2 : 6>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
   all_axes<Q, 0, R, HEQ ? 2 : 6>(st.Mh, ux, uy, uz);  // raw -> central
   if constexpr (!HEQ) cumulant_high<Q, true>(st.Mh);   // central -> cumulant (orders 4..6)
@@ -814,9 +858,9 @@ __device__ __forceinline__ void collide_k_impl(R (&f)[Q], const CP<R>& p) {
   store_moments<Q, R, SH>(st.Mh, st, f);
 }
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_k(R (&f)[Q], const CP<R>& p) {
-  if (p.omega_high == R(1)) collide_k_impl<Q, R, SH, true>(f, p);
-  else collide_k_impl<Q, R, SH, false>(f, p);
+__device__ __forceinline__ void collide_k(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if (p.omega_high == R(1)) collide_k_impl<Q, R, SH, true>(f, p, cs);
+  else collide_k_impl<Q, R, SH, false>(f, p, cs);
 }
 
 // Recursive regularized (Hermite form): second-order non-equilibrium Hermite
@@ -824,9 +868,10 @@ __device__ __forceinline__ void collide_k(R (&f)[Q], const CP<R>& p) {
 // post-collision second-order non-equilibrium a2*:
 //   a_pqr = C(p,2) u^(p-2,q,r) a_xx + C(q,2) ... + p q u^(p-1,q-1,r) a_xy + ...
 template <int Q, typename R, bool SH>
-__device__ __forceinline__ void collide_rr(R (&f)[Q], const CP<R>& p) {
+__device__ __forceinline__ void collide_rr(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
   MomState<Q, R, SH> st;
   load_moments<Q, R, SH>(f, st);
+  cell_sums<R, SH>(cs, st.drho, st.ux, st.uy, st.uz);
   const R ux = st.ux, uy = st.uy, uz = st.uz;
   const R cs2 = R(1.0 / 3.0);
 #define IX(a, b, c) bidx<Q, a, b, c>
@@ -883,18 +928,20 @@ __device__ __forceinline__ void collide_rr(R (&f)[Q], const CP<R>& p) {
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
+// cs (optional): receives the cell's share of the conserved sums, computed from
+// the pre-collision moments
 template <int Q, int M, typename R, bool SH>
-__device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p) {
-  if constexpr (M == BGK_W2) collide_bgk_w2<Q, R, SH>(f, p);
-  else if constexpr (M == BGK_NW4) collide_nw4<Q, R, SH>(f, p);
-  else if constexpr (M == TRT) collide_trt<Q, R, SH>(f, p);
-  else if constexpr (M == REG) collide_reg<Q, R, SH>(f, p);
-  else if constexpr (M == RR) collide_rr<Q, R, SH>(f, p);
-  else if constexpr (M == RM) collide_rm<Q, R, SH>(f, p);
-  else if constexpr (M == HM) collide_hm<Q, R, SH>(f, p);
-  else if constexpr (M == CM) collide_cm<Q, R, SH>(f, p);
-  else if constexpr (M == CHM) collide_chm<Q, R, SH>(f, p);
-  else collide_k<Q, R, SH>(f, p);
+__device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if constexpr (M == BGK_W2) collide_bgk_w2<Q, R, SH>(f, p, cs);
+  else if constexpr (M == BGK_NW4) collide_nw4<Q, R, SH>(f, p, cs);
+  else if constexpr (M == TRT) collide_trt<Q, R, SH>(f, p, cs);
+  else if constexpr (M == REG) collide_reg<Q, R, SH>(f, p, cs);
+  else if constexpr (M == RR) collide_rr<Q, R, SH>(f, p, cs);
+  else if constexpr (M == RM) collide_rm<Q, R, SH>(f, p, cs);
+  else if constexpr (M == HM) collide_hm<Q, R, SH>(f, p, cs);
+  else if constexpr (M == CM) collide_cm<Q, R, SH>(f, p, cs);
+  else if constexpr (M == CHM) collide_chm<Q, R, SH>(f, p, cs);
+  else collide_k<Q, R, SH>(f, p, cs);
 }
 
 // the model's own equilibrium of (rho, u), in stored form (shifted or not);

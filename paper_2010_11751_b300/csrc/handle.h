@@ -32,6 +32,9 @@ struct lbm_s {
   int threads = 256;
   lbm::StepFn fns[lbm::NUM_STEP_KINDS] = {};
   lbm::StagedFn sfns[2] = {};  // staged AA even / odd steps, or null (one-thread-per-cell kernels)
+  lbm::StepSumFn sumfns[lbm::NUM_STEP_KINDS] = {};  // summing step kernels (SoA), or null
+  double* d_sum_partials = nullptr;                 // their per-block partial sums
+  size_t sum_partials_cap = 0;                      // doubles allocated there
   int* d_err = nullptr;        // [0] error word of the staged kernels, [1] scratch counter
   // fluid cells with a non-zero flag byte (staged steps), sorted, and their records
   int* d_list = nullptr;

@@ -15,6 +15,9 @@ struct BatchArgs;
 constexpr int RUN_ALIGN_BYTES = 128;
 constexpr size_t STAGE_PAD_BYTES = RUN_ALIGN_BYTES;
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
+// step kernel that also writes per-block FP64 partial sums (mass, kinetic
+// energy) of the state it reads: partials[2 b], partials[2 b + 1] for block b
+using StepSumFn = cudaError_t (*)(const KArgs&, int threads, double* partials, cudaStream_t);
 using BatchFn = cudaError_t (*)(const BatchArgs&, int sk, int blocks, int threads, cudaStream_t);
 // the fluid cells that are not bulk cells (flag byte non-zero), sorted, with a
 // record each: solid-neighbour mask | domain-face bit << 31, and the wall kind
@@ -32,6 +35,8 @@ using StagedFn = cudaError_t (*)(const KArgs&, int* err, const Listed& listed, c
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);
+// summing step kernel for the same key (SoA only); nullptr if not built
+StepSumFn step_sum_fn(int model, int Q, int P, int L, int SK);
 // batched AA kernel (SoA) for (lattice, model, precision); nullptr if not built
 BatchFn batch_fn(int model, int Q, int P);
 // staged AA step (SoA) for (lattice, model, precision, K_AA_EVEN / K_AA_ODD);
@@ -47,6 +52,8 @@ cudaError_t launch_set(int Q, int P, int L, int LD, const KArgs& a, const double
 cudaError_t launch_init(int Q, int P, int L, int LD, bool nw4, const KArgs& a, const double* rho, const double* u,
                         cudaStream_t s);
 int reduce_partials_count(int N);
+// out[0], out[1] = the sums of the n pairs of partials, in a fixed order
+cudaError_t launch_reduce_final(const double* partials, int n, double* out, cudaStream_t s);
 cudaError_t launch_reduce(int Q, int P, int L, int LD, const KArgs& a, double* partials, double* out2,
                           cudaStream_t s);
 cudaError_t launch_swap_stream(int Q, int P, int L, const KArgs& a, int threads, cudaStream_t s);

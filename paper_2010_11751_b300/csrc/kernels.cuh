@@ -27,6 +27,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "collision.cuh"
 
 namespace lbm {
@@ -337,8 +339,10 @@ __device__ __forceinline__ CP<typename Store<P>::R> rates(const KArgs& a) {
 // rate_fn() yields the relaxation rates; it is called just before the
 // collision, so that a single-lattice kernel reads them from its launch
 // parameters without holding registers across the loads
+// cs (optional): receives the cell's share of the conserved sums of the state
+// it reads; left untouched for a solid cell
 template <int Q, int M, int P, int L, int SK, class RateFn>
-__device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn) {
+__device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn, CellSums* cs = nullptr) {
   using R = typename Store<P>::R;
   R f[Q];
   uint8_t fl;
@@ -356,7 +360,7 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
     else step_load<Q, P, L, SK, false>(a, i, f, fl);
   }
   const CP<R> cp = rate_fn();
-  collide<Q, M, R, Store<P>::shifted>(f, cp);
+  collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
   if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
   else step_store<Q, P, L, SK, false>(a, i, f, fl);
 }
@@ -382,6 +386,70 @@ __global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_kernel(KArgs a)
 }
 
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
+
+using StepSumFn = cudaError_t (*)(const KArgs&, int threads, double* partials, cudaStream_t);
+
+// a step kernel that also sums, over its block, the FP64 mass and kinetic
+// energy of the fluid cells it reads (the collision's own moments), and writes
+// them to partials[2 * block], partials[2 * block + 1] in a fixed order
+template <int Q, int M, int P, int L, int SK>
+__global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_sum_kernel(KArgs a, double* partials) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  CellSums cs{0.0, 0.0};
+  if (i < a.N) step_one<Q, M, P, L, SK>(a, i, [&] { return rates<P>(a); }, &cs);
+  double m = cs.rho, e = cs.ke;
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_down_sync(0xffffffffu, m, o);
+    e += __shfl_down_sync(0xffffffffu, e, o);
+  }
+  __shared__ double sm[8][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sm[w][0] = m;
+    sm[w][1] = e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tm = 0.0, te = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      tm += sm[k][0];
+      te += sm[k][1];
+    }
+    partials[2 * blockIdx.x] = tm;
+    partials[2 * blockIdx.x + 1] = te;
+  }
+}
+
+template <int Q, int M, int P, int L, int SK>
+cudaError_t launch_step_sum(const KArgs& a, int threads, double* partials, cudaStream_t s) {
+  const int blocks = (a.N + threads - 1) / threads;
+  step_sum_kernel<Q, M, P, L, SK><<<blocks, threads, 0, s>>>(a, partials);
+  return cudaGetLastError();
+}
+
+// summing step kernels of one model (SoA; every lattice, storage and step kind)
+template <int M>
+StepSumFn step_sum_fn_for_model(int Q, int P, int L, int SK) {
+  if (L != SOA) return nullptr;
+  auto pick = [&](auto q, auto pp) -> StepSumFn {
+    constexpr int QQ = decltype(q)::value, PP = decltype(pp)::value;
+    switch (SK) {
+      case K_TWOPOP: return &launch_step_sum<QQ, M, PP, SOA, K_TWOPOP>;
+      case K_AA_EVEN: return &launch_step_sum<QQ, M, PP, SOA, K_AA_EVEN>;
+      case K_AA_ODD: return &launch_step_sum<QQ, M, PP, SOA, K_AA_ODD>;
+      case K_ESOTWIST: return &launch_step_sum<QQ, M, PP, SOA, K_ESOTWIST>;
+      default: return nullptr;
+    }
+  };
+  using I19 = std::integral_constant<int, 19>;
+  using I27 = std::integral_constant<int, 27>;
+  using PF64 = std::integral_constant<int, F64>;
+  using PF32 = std::integral_constant<int, F32>;
+  using PF16 = std::integral_constant<int, F16>;
+  if (Q == 19) return P == F64 ? pick(I19{}, PF64{}) : (P == F32 ? pick(I19{}, PF32{}) : (P == F16 ? pick(I19{}, PF16{}) : nullptr));
+  if (Q == 27) return P == F64 ? pick(I27{}, PF64{}) : (P == F32 ? pick(I27{}, PF32{}) : (P == F16 ? pick(I27{}, PF16{}) : nullptr));
+  return nullptr;
+}
 
 template <int Q, int M, int P, int L, int SK>
 cudaError_t launch_step(const KArgs& a, int threads, cudaStream_t s) {

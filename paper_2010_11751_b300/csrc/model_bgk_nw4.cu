@@ -10,4 +10,5 @@ namespace lbm {
 StepFn step_fn_bgk_nw4(int Q, int P, int L, int SK) { return step_fn_for_model<BGK_NW4>(Q, P, L, SK); }
 BatchFn batch_fn_bgk_nw4(int Q, int P) { return batch_fn_for_model<BGK_NW4>(Q, P); }
 StagedFn staged_fn_bgk_nw4(int Q, int P, int SK) { return staged_fn_for_model<BGK_NW4>(Q, P, SK); }
+StepSumFn step_sum_fn_bgk_nw4(int Q, int P, int L, int SK) { return step_sum_fn_for_model<BGK_NW4>(Q, P, L, SK); }
 }  // namespace lbm

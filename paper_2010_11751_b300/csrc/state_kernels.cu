@@ -362,6 +362,11 @@ cudaError_t launch_reduce(int Q, int P, int L, int LD, const KArgs& a, double* p
   return cudaGetLastError();
 }
 
+cudaError_t launch_reduce_final(const double* partials, int n, double* out, cudaStream_t s) {
+  reduce_final_kernel<<<1, 1024, 0, s>>>(partials, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_swap_stream(int Q, int P, int L, const KArgs& a, int threads, cudaStream_t s) {
   return dispatch_qpl(Q, P, L, [&](auto q, auto p, auto l) {
     LBM_CONSTS(q, p, l);

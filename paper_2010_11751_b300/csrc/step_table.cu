@@ -26,6 +26,16 @@ BatchFn batch_fn_cm(int, int);
 BatchFn batch_fn_chm(int, int);
 BatchFn batch_fn_k(int, int);
 
+StepSumFn step_sum_fn_bgk_w2(int, int, int, int);
+StepSumFn step_sum_fn_bgk_nw4(int, int, int, int);
+StepSumFn step_sum_fn_trt(int, int, int, int);
+StepSumFn step_sum_fn_reg(int, int, int, int);
+StepSumFn step_sum_fn_rr(int, int, int, int);
+StepSumFn step_sum_fn_rm(int, int, int, int);
+StepSumFn step_sum_fn_hm(int, int, int, int);
+StepSumFn step_sum_fn_cm(int, int, int, int);
+StepSumFn step_sum_fn_chm(int, int, int, int);
+StepSumFn step_sum_fn_k(int, int, int, int);
 StagedFn staged_fn_bgk_w2(int, int, int);
 StagedFn staged_fn_bgk_nw4(int, int, int);
 StagedFn staged_fn_trt(int, int, int);
@@ -79,6 +89,21 @@ StagedFn staged_fn(int model, int Q, int P, int SK) {
     case CM: return staged_fn_cm(Q, P, SK);
     case CHM: return staged_fn_chm(Q, P, SK);
     case KUM: return staged_fn_k(Q, P, SK);
+    default: return nullptr;
+  }
+}
+StepSumFn step_sum_fn(int model, int Q, int P, int L, int SK) {
+  switch (model) {
+    case BGK_W2: return step_sum_fn_bgk_w2(Q, P, L, SK);
+    case BGK_NW4: return step_sum_fn_bgk_nw4(Q, P, L, SK);
+    case TRT: return step_sum_fn_trt(Q, P, L, SK);
+    case REG: return step_sum_fn_reg(Q, P, L, SK);
+    case RR: return step_sum_fn_rr(Q, P, L, SK);
+    case RM: return step_sum_fn_rm(Q, P, L, SK);
+    case HM: return step_sum_fn_hm(Q, P, L, SK);
+    case CM: return step_sum_fn_cm(Q, P, L, SK);
+    case CHM: return step_sum_fn_chm(Q, P, L, SK);
+    case KUM: return step_sum_fn_k(Q, P, L, SK);
     default: return nullptr;
   }
 }

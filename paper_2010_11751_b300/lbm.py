@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         "lbm_device_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
         "lbm_bytes_per_cell_update": [vp, ctypes.POINTER(d)],
         "lbm_kernels_per_step": [vp, ctypes.POINTER(i)],
+        "lbm_step_sums": [vp, i, ctypes.POINTER(d), ctypes.POINTER(d)],
         "lbm_destroy": [vp],
         "lbm_supported": [i, i, i, i, i],
         "lbm_conserved_sums_static": [i, i, dp, u8p, dp, vp],
@@ -183,6 +184,12 @@ def lbm_bytes_per_cell_update(h):
     v = ctypes.c_double()
     _check(lib().lbm_bytes_per_cell_update(h, ctypes.byref(v)))
     return v.value
+
+
+def lbm_step_sums(h, n):
+    m, e = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lbm_step_sums(h, n, ctypes.byref(m), ctypes.byref(e)))
+    return m.value, e.value
 
 
 def lbm_kernels_per_step(h):
@@ -314,6 +321,10 @@ class Lattice:
         if isinstance(f, np.ndarray):
             f = np.ascontiguousarray(f, dtype=np.float64)
         lbm_set_populations(self.h, f)
+
+    def step_sums(self, n=1):
+        """(mass, energy) of the current state, then n steps: lbm_step_sums."""
+        return lbm_step_sums(self.h, n)
 
     def reduce(self):
         return lbm_reduce(self.h)

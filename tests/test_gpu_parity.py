@@ -218,3 +218,45 @@ def test_divergence_is_reported(scheme):
         g.set_populations(f0)
         g.step(2)
         g.reduce()  # finite state: no error
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+@pytest.mark.parametrize("model", ["BGK_W2", "TRT", "REG", "RR", "K"])
+def test_step_sums_is_reduce_then_step(Q, scheme, model):
+    """lbm_step_sums(n): the FP64 sums of the starting state (as lbm_reduce gives them, up to
+    summation order) and the same populations as lbm_step(n), bit for bit, at both parities."""
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=151, model=model)
+    for pre in (0, 1):
+        with gpu_lattice(Q, DIMS, flags, model, p, scheme) as g:
+            g.set_populations(f0)
+            g.step(pre)
+            m0, e0 = g.reduce()
+            g.step(3)
+            want = g.get_populations().copy()
+        with gpu_lattice(Q, DIMS, flags, model, p, scheme) as g:
+            g.set_populations(f0)
+            g.step(pre)
+            m, e = g.step_sums(3)
+            got = g.get_populations().copy()
+        assert np.array_equal(got, want), (scheme, pre)
+        assert abs(m - m0) <= 1e-13 * m0 and abs(e - e0) <= 1e-12 * e0, (m, m0, e, e0)
+
+
+def test_step_sums_fallback_and_zero_steps():
+    """AoS has no summing kernel: lbm_step_sums runs the reduction, then the steps; n = 0 is
+    lbm_reduce."""
+    Q, p = 19, prm()
+    flags, f0 = case(Q, DIMS, seed=161)
+    with gpu_lattice(Q, DIMS, flags, "TRT", p, "aa", layout=L.AOS) as g:
+        g.set_populations(f0)
+        m0, e0 = g.reduce()
+        assert g.step_sums(0) == (m0, e0)
+        assert g.step_sums(2) == (m0, e0)  # the same reduction kernel: identical sums
+        assert g.steps_done == 2
+        m2, e2 = g.reduce()
+    with gpu_lattice(Q, DIMS, flags, "TRT", p, "aa") as g:
+        g.set_populations(f0)
+        g.step(2)
+        assert g.reduce() == (m2, e2)

@@ -89,3 +89,30 @@ def test_cavity_re1000_2000_steps_budget(precision, budget):
         _, ug = g.macroscopic()
     err = _l2_rel(ug, u_ref, flags == 0)
     assert err <= budget, err
+
+
+@pytest.mark.parametrize("precision", [L.F32, L.F16])
+@pytest.mark.parametrize("scheme", ["twopop", "aa", "esotwist"])
+def test_step_sums_shifted_storage(precision, scheme):
+    """Shifted storage: each cell's share of the sums is formed in FP32 (mass from the FP32
+    density deviation), accumulated in FP64; populations as lbm_step's, bit for bit. The staged
+    FP16 AA step has no summing kernel and uses the reduction kernel (identical sums)."""
+    Q, p = 19, prm()
+    flags, f0 = case(Q, DIMS, seed=171, model="TRT")
+    with L.Lattice(Q, *DIMS, scheme, "TRT", p["omega"], flags, precision=precision, wall_velocities=WALLS,
+                   trt_lambda=p["trt_lambda"]) as g:
+        g.set_populations(f0)
+        m0, e0 = g.reduce()
+        g.step(3)
+        want = g.get_populations().copy()
+    with L.Lattice(Q, *DIMS, scheme, "TRT", p["omega"], flags, precision=precision, wall_velocities=WALLS,
+                   trt_lambda=p["trt_lambda"]) as g:
+        g.set_populations(f0)
+        m, e = g.step_sums(3)
+        got = g.get_populations().copy()
+    assert np.array_equal(got, want)
+    # a cell's density deviation is a sum of 19 FP32 values of size <= 1: its rounding, at most
+    # a few FP32 ulps of 1 per cell, bounds the relative mass difference by ~1e-7 (FP64 sums of
+    # the same FP32-stored values agree far closer in practice)
+    assert abs(m - m0) <= 1e-7 * m0
+    assert abs(e - e0) <= 2e-6 * e0
