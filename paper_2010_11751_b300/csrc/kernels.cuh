@@ -42,7 +42,8 @@ struct KArgs {
   void* a;                // populations (current state)
   void* b;                // destination array of the two-population scheme
   const uint8_t* flags;   // classified flag bytes
-  const uint32_t* nbmask; // per fluid cell: bit k set when the neighbour along c_k is solid
+  const uint32_t* nbmask; // per fluid cell: bit k set when the neighbour along c_k is solid (k < 27);
+                          // NBMASK_UNIFORM: all those neighbours share the wall kind in bits 27-29
   const double* wall;     // wall term table [8][Q]: -6 t_k c_k.u_w(kind)
   int nx, ny, nz, N;
   int parity;             // time-step parity (esoteric twist slot labels)
@@ -160,9 +161,11 @@ struct Nb {
     if constexpr (FAST) return false;
     else return ((mask >> K) & 1u) != 0;
   }
-  // wall kind of a solid neighbour along c_k (reads its flag byte)
+  // wall kind of a solid neighbour along c_k: from the mask word when all the
+  // cell's solid neighbours share one kind, else from the neighbour's flag byte
   template <int Q, int K>
   __device__ __forceinline__ int kind() const {
+    if (mask & NBMASK_UNIFORM) return (int)((mask >> NBMASK_KIND_SHIFT) & FLAG_KIND);
     return flags[at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>()] & FLAG_KIND;
   }
   template <int Q, int K>

@@ -126,5 +126,9 @@ struct Store<F16> {
 constexpr uint8_t FLAG_KIND = 0x07;
 constexpr uint8_t FLAG_EDGE = 0x40;
 constexpr uint8_t FLAG_NEARWALL = 0x80;
+// solid-neighbour mask word of a fluid cell: bits 0..26 one per link; bit 30
+// set when every solid neighbour has the same wall kind, stored in bits 27..29
+constexpr uint32_t NBMASK_UNIFORM = 1u << 30;
+constexpr int NBMASK_KIND_SHIFT = 27;
 
 }  // namespace lbm

@@ -20,16 +20,25 @@ __global__ void classify_kernel(const uint8_t* __restrict__ raw, uint8_t* __rest
   uint8_t v = raw[i] & FLAG_KIND;
   if (v == 0) {
     if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1) v |= FLAG_EDGE;
-    uint32_t mask = 0u;
+    uint32_t mask = 0u, kind0 = 0u;
+    bool uniform = true;
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       int xn = x + Lat<Q>::c(k, 0), yn = y + Lat<Q>::c(k, 1), zn = z + Lat<Q>::c(k, 2);
       xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
       yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
       zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
-      if (raw[(xn * ny + yn) * nz + zn] & FLAG_KIND) mask |= 1u << k;
+      const uint32_t kind = raw[(xn * ny + yn) * nz + zn] & FLAG_KIND;
+      if (kind) {
+        mask |= 1u << k;
+        if (kind0 == 0u) kind0 = kind;
+        else if (kind != kind0) uniform = false;
+      }
     });
     if (mask) v |= FLAG_NEARWALL;
+    // every solid neighbour of one wall kind (the common case): the kind rides in
+    // the mask word, so that stores need no neighbour flag byte
+    if (mask && uniform) mask |= NBMASK_UNIFORM | (kind0 << NBMASK_KIND_SHIFT);
     mask_out[i] = mask;
   } else {
     mask_out[i] = 0u;
