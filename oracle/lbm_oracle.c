@@ -53,6 +53,16 @@
  * lexicographically (-1 < 0 < 1), then the rest vector, then the negated
  * first half.  This gives c_0 = (-1,0,0) = -c_10 for D3Q19 (Section 2.6).
  *
+ * Pins (tests/test_oracle_*.py, against what the mathematics fixes, not
+ * against this file): worked inversion example and equilibrium symmetry of
+ * Section 2.6; exact mass and momentum conservation; equilibrium as a fixed
+ * point; omega = 1 gives the equilibrium; each model's per-moment relaxation
+ * law recomputed independently; reductions of RM, HM, CM, CHM to BGK_NW4 at
+ * equal rates; cumulants against log-moment-generating-function derivatives;
+ * Couette and TRT Poiseuille exactness, Taylor-Green decay and its order of
+ * convergence; hand-enumerated pulls on tiny lattices; traversal-order
+ * independence.  No function here is parity unpinned.
+ *
  * Compile with -ffp-contract=off so that each operation rounds once.
  */
 #include <math.h>
