@@ -84,7 +84,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--forms", default="", help="precision: FP32/FP16 shifted storage at 512^3 vs FP64")
+    ap.add_argument("--forms", default="",
+                    help="precision | batching | serving | sweep | unrolling: the forms and studies besides "
+                         "the headline")
     ap.add_argument("--form-steps", type=int, default=2000)
     ap.add_argument("--trace", type=int, default=500, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrival rate (1/s)")
@@ -530,8 +532,49 @@ def size_sweep(args):
     return rows
 
 
+def unrolling_form(args):
+    """The loop-unrolling study of Section 4 (BGK-W2, AA-SoA, N = 128, and here 256 too): the
+    unrolled BGK-W2 kernels against BGK-W2 in the educational form (loops over the directions,
+    tabulated c_k and t_k), compiled as the compiler chooses, and with the loops kept rolled."""
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    rows = []
+    for prec in ("f64", "f32"):
+        for n in (128, 256):
+            args.n = n
+            _, omega, flags, walls = workload(args)
+            for coll in ("BGK_W2", "BGK_W2_EDU", "BGK_W2_LOOP"):
+                stream = torch.cuda.Stream()
+                g = L.Lattice(19, n, n, n, "aa", coll, omega, flags, precision=L.PRECISIONS[prec],
+                              wall_velocities=walls, stream=stream.cuda_stream)
+                g.init_equilibrium()
+                steps = 200 if prec == "f32" else 50
+                g.step(6)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                g.step(steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                rows.append({"precision": prec, "n": n, "collision": coll, "steps": steps,
+                             "mlups": round(n ** 3 / (ms * 1e-3) / 1e6, 1)})
+                g.close()
+    for r in rows:
+        base = next(b for b in rows if b["precision"] == r["precision"] and b["n"] == r["n"]
+                    and b["collision"] == "BGK_W2")
+        r["unrolled_speedup"] = round(base["mlups"] / r["mlups"], 3)
+    return rows
+
+
 def main():
     args = parse()
+    if args.forms == "unrolling":
+        print(json.dumps({"form": "unrolling", "config": "D3Q19 cavity, AA, SoA, BGK-W2 unrolled vs educational",
+                          "rows": unrolling_form(args)}))
+        return
     if args.forms == "sweep":
         print(json.dumps({"form": "size_sweep", "precision": args.precision, "rows": size_sweep(args)}))
         return

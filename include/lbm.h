@@ -87,6 +87,12 @@ extern "C" {
 #define LBM_CM 7      /* central-moment multi-relaxation */
 #define LBM_CHM 8     /* central-Hermite-moment multi-relaxation */
 #define LBM_K 9       /* cumulant */
+/* BGK-W2 again, in the "educational" form of Section 2.6 (one plain loop over
+ * the directions with tabulated c_k, t_k; only the density and velocity sums
+ * regrouped), for the unrolled-versus-educational comparison of Section 4:
+ * loops as the compiler chooses to compile them, or kept rolled. */
+#define LBM_BGK_W2_EDU 10
+#define LBM_BGK_W2_LOOP 11
 
 /* ---- layouts (Section 2.3) ---- */
 #define LBM_SOA 0 /* pop[Q][N] */

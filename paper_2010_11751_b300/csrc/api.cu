@@ -204,7 +204,9 @@ int load_kind(const lbm_s* h) {
 
 int store_kind(const lbm_s* h) { return h->scheme == LBM_ESOTWIST ? LD_ET_EVEN : LD_LOCAL; }
 
-bool nw4_equilibrium(int model) { return !(model == BGK_W2 || model == TRT || model == REG); }
+bool nw4_equilibrium(int model) {
+  return !(model == BGK_W2 || model == TRT || model == REG || model == BGK_W2_EDU || model == BGK_W2_LOOP);
+}
 
 int reset_populations(lbm_s* h) {
   int rc = ensure_alloc(h);

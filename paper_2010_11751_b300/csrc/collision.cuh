@@ -19,8 +19,12 @@
 
 namespace lbm {
 
-enum Model : int { BGK_W2 = 0, BGK_NW4 = 1, TRT = 2, REG = 3, RR = 4, RM = 5, HM = 6, CM = 7, CHM = 8, KUM = 9 };
-constexpr int NUM_MODELS = 10;
+enum Model : int {
+  BGK_W2 = 0, BGK_NW4 = 1, TRT = 2, REG = 3, RR = 4, RM = 5, HM = 6, CM = 7, CHM = 8, KUM = 9,
+  // BGK-W2 in the educational form of Section 2.6 (see collide_bgk_w2_edu)
+  BGK_W2_EDU = 10, BGK_W2_LOOP = 11
+};
+constexpr int NUM_MODELS = 12;
 
 // relaxation parameters, prepared on the host
 template <typename R>
@@ -537,6 +541,80 @@ __device__ __forceinline__ void collide_trt(R (&f)[Q], const CP<R>& p, CellSums*
   }
 }
 
+// ---------------------------------------------------------------------------
+// BGK-W2 in the "educational" form of Section 2.6: density and velocity from
+// regrouped partial sums (as above), then one plain loop over the first half
+// of the directions that reads c_k and t_k from a table, forms E_k from its
+// defining formula and the opposite equilibrium from the symmetry
+// E_kbar = E_k - 6 rho t_k c_k.u, and relaxes both populations.  Nothing in
+// the loop is unrolled or regrouped by hand.  ROLLED keeps the loop rolled
+// (#pragma unroll 1, so f lives in local memory); otherwise the compiler
+// decides.  Same equations as collide_bgk_w2, other rounding order.
+// ---------------------------------------------------------------------------
+template <int Q>
+struct EduTable {
+  int c[Q][3];
+  double t[Q];
+};
+template <int Q>
+constexpr EduTable<Q> make_edu_table() {
+  EduTable<Q> T{};
+  for (int k = 0; k < Q; ++k) {
+    for (int d = 0; d < 3; ++d) T.c[k][d] = Lat<Q>::c(k, d);
+    T.t[k] = Lat<Q>::w(k);
+  }
+  return T;
+}
+static __constant__ EduTable<19> edu_table19 = make_edu_table<19>();
+static __constant__ EduTable<27> edu_table27 = make_edu_table<27>();
+template <int Q>
+__device__ __forceinline__ const EduTable<Q>& edu_table() {
+  if constexpr (Q == 19) return edu_table19;
+  else return edu_table27;
+}
+
+template <int Q, typename R, bool SH, bool ROLLED>
+__device__ __forceinline__ void collide_bgk_w2_edu(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  constexpr int H = Lat<Q>::H;
+  R s[H], d[H];
+  pair_sums<Q>(f, s, d);
+  R r = f[H], jx = R(-0.0), jy = R(-0.0), jz = R(-0.0);
+  static_for<0, H>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    r = r + s[k];
+    jx = addc<Lat<Q>::e(k, 0)>(jx, d[k]);
+    jy = addc<Lat<Q>::e(k, 1)>(jy, d[k]);
+    jz = addc<Lat<Q>::e(k, 2)>(jz, d[k]);
+  });
+  const R rho = SH ? R(1) + r : r;
+  const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
+  const R usq = ux * ux + uy * uy + uz * uz;
+  cell_sums<R, SH>(cs, r, ux, uy, uz);
+  const EduTable<Q>& T = edu_table<Q>();
+  const R omega = p.omega;
+  // rest population: E = rho t (1 - 1.5 |u|^2)
+  {
+    const R t = R(T.t[H]);
+    const R E = rho * t * (R(1) - R(1.5) * usq) - (SH ? t : R(0));
+    f[H] = f[H] + omega * (E - f[H]);
+  }
+  auto pair = [&](int k) {
+    const R t = R(T.t[k]);
+    const R cu = R(T.c[k][0]) * ux + R(T.c[k][1]) * uy + R(T.c[k][2]) * uz;
+    const R Ek = rho * t * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+    const R Ekb = Ek - R(6) * rho * t * cu;
+    const R shift = SH ? t : R(0);
+    f[k] = f[k] + omega * ((Ek - shift) - f[k]);
+    f[k + H + 1] = f[k + H + 1] + omega * ((Ekb - shift) - f[k + H + 1]);
+  };
+  if constexpr (ROLLED) {
+#pragma unroll 1
+    for (int k = 0; k < H; ++k) pair(k);
+  } else {
+    for (int k = 0; k < H; ++k) pair(k);
+  }
+}
+
 // Regularized: f_out = E + (1 - w) t_k/(2 cs^4) H2_k : Pi_neq,
 // Pi_neq = sum_k c c (f - E); W2 equilibrium.
 template <int Q, typename R, bool SH>
@@ -941,6 +1019,8 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p, CellSums* cs 
   else if constexpr (M == HM) collide_hm<Q, R, SH>(f, p, cs);
   else if constexpr (M == CM) collide_cm<Q, R, SH>(f, p, cs);
   else if constexpr (M == CHM) collide_chm<Q, R, SH>(f, p, cs);
+  else if constexpr (M == BGK_W2_EDU) collide_bgk_w2_edu<Q, R, SH, false>(f, p, cs);
+  else if constexpr (M == BGK_W2_LOOP) collide_bgk_w2_edu<Q, R, SH, true>(f, p, cs);
   else collide_k<Q, R, SH>(f, p, cs);
 }
 
@@ -950,7 +1030,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p, CellSums* cs 
 template <int Q, int M, typename R, bool SH>
 __device__ __forceinline__ void equilibrium(R rho, R drho, R ux, R uy, R uz, R (&f)[Q]) {
   constexpr int H = Lat<Q>::H;
-  if constexpr (M == BGK_W2 || M == TRT || M == REG) {
+  if constexpr (M == BGK_W2 || M == TRT || M == REG || M == BGK_W2_EDU || M == BGK_W2_LOOP) {
     const R usq = ux * ux + uy * uy + uz * uz;
     const R A = SH ? drho - R(1.5) * rho * usq : rho * (R(1) - R(1.5) * usq);
     f[H] = R(WGT<Q, H>) * A;

@@ -14,6 +14,8 @@ StepFn step_fn_hm(int, int, int, int);
 StepFn step_fn_cm(int, int, int, int);
 StepFn step_fn_chm(int, int, int, int);
 StepFn step_fn_k(int, int, int, int);
+StepFn step_fn_bgk_w2_loop(int, int, int, int);
+StepFn step_fn_bgk_w2_edu(int, int, int, int);
 
 BatchFn batch_fn_bgk_w2(int, int);
 BatchFn batch_fn_bgk_nw4(int, int);
@@ -25,6 +27,8 @@ BatchFn batch_fn_hm(int, int);
 BatchFn batch_fn_cm(int, int);
 BatchFn batch_fn_chm(int, int);
 BatchFn batch_fn_k(int, int);
+BatchFn batch_fn_bgk_w2_loop(int, int);
+BatchFn batch_fn_bgk_w2_edu(int, int);
 
 StepSumFn step_sum_fn_bgk_w2(int, int, int, int);
 StepSumFn step_sum_fn_bgk_nw4(int, int, int, int);
@@ -36,6 +40,8 @@ StepSumFn step_sum_fn_hm(int, int, int, int);
 StepSumFn step_sum_fn_cm(int, int, int, int);
 StepSumFn step_sum_fn_chm(int, int, int, int);
 StepSumFn step_sum_fn_k(int, int, int, int);
+StepSumFn step_sum_fn_bgk_w2_loop(int, int, int, int);
+StepSumFn step_sum_fn_bgk_w2_edu(int, int, int, int);
 StagedFn staged_fn_bgk_w2(int, int, int);
 StagedFn staged_fn_bgk_nw4(int, int, int);
 StagedFn staged_fn_trt(int, int, int);
@@ -46,6 +52,8 @@ StagedFn staged_fn_hm(int, int, int);
 StagedFn staged_fn_cm(int, int, int);
 StagedFn staged_fn_chm(int, int, int);
 StagedFn staged_fn_k(int, int, int);
+StagedFn staged_fn_bgk_w2_loop(int, int, int);
+StagedFn staged_fn_bgk_w2_edu(int, int, int);
 
 StepFn step_fn(int model, int Q, int P, int L, int SK) {
   switch (model) {
@@ -59,6 +67,8 @@ StepFn step_fn(int model, int Q, int P, int L, int SK) {
     case CM: return step_fn_cm(Q, P, L, SK);
     case CHM: return step_fn_chm(Q, P, L, SK);
     case KUM: return step_fn_k(Q, P, L, SK);
+    case BGK_W2_LOOP: return step_fn_bgk_w2_loop(Q, P, L, SK);
+    case BGK_W2_EDU: return step_fn_bgk_w2_edu(Q, P, L, SK);
     default: return nullptr;
   }
 }
@@ -74,6 +84,8 @@ BatchFn batch_fn(int model, int Q, int P) {
     case CM: return batch_fn_cm(Q, P);
     case CHM: return batch_fn_chm(Q, P);
     case KUM: return batch_fn_k(Q, P);
+    case BGK_W2_LOOP: return batch_fn_bgk_w2_loop(Q, P);
+    case BGK_W2_EDU: return batch_fn_bgk_w2_edu(Q, P);
     default: return nullptr;
   }
 }
@@ -89,6 +101,8 @@ StagedFn staged_fn(int model, int Q, int P, int SK) {
     case CM: return staged_fn_cm(Q, P, SK);
     case CHM: return staged_fn_chm(Q, P, SK);
     case KUM: return staged_fn_k(Q, P, SK);
+    case BGK_W2_LOOP: return staged_fn_bgk_w2_loop(Q, P, SK);
+    case BGK_W2_EDU: return staged_fn_bgk_w2_edu(Q, P, SK);
     default: return nullptr;
   }
 }
@@ -104,6 +118,8 @@ StepSumFn step_sum_fn(int model, int Q, int P, int L, int SK) {
     case CM: return step_sum_fn_cm(Q, P, L, SK);
     case CHM: return step_sum_fn_chm(Q, P, L, SK);
     case KUM: return step_sum_fn_k(Q, P, L, SK);
+    case BGK_W2_LOOP: return step_sum_fn_bgk_w2_loop(Q, P, L, SK);
+    case BGK_W2_EDU: return step_sum_fn_bgk_w2_edu(Q, P, L, SK);
     default: return nullptr;
   }
 }

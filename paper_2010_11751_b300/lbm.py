@@ -21,9 +21,9 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_STATE, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ER
 D3Q19, D3Q27 = 19, 27
 TWOPOP, SWAP, AA, ESOTWIST = 0, 1, 2, 3
 SCHEMES = {"twopop": TWOPOP, "swap": SWAP, "aa": AA, "esotwist": ESOTWIST}
-BGK_W2, BGK_NW4, TRT, REG, RR, RM, HM, CM, CHM, K = range(10)
+BGK_W2, BGK_NW4, TRT, REG, RR, RM, HM, CM, CHM, K, BGK_W2_EDU, BGK_W2_LOOP = range(12)
 MODELS = {"BGK_W2": BGK_W2, "BGK_NW4": BGK_NW4, "TRT": TRT, "REG": REG, "RR": RR, "RM": RM, "HM": HM, "CM": CM,
-          "CHM": CHM, "K": K}
+          "CHM": CHM, "K": K, "BGK_W2_EDU": BGK_W2_EDU, "BGK_W2_LOOP": BGK_W2_LOOP}
 SOA, AOS = 0, 1
 F64, F32, F16 = 0, 1, 2
 PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}

@@ -59,11 +59,11 @@ def test_null_handles_rejected(L):
 def test_supported_combinations(L):
     for Q in (19, 27):
         for s in range(4):
-            for m in range(10):
+            for m in range(12):  # ten models, plus BGK-W2 in its two educational forms
                 assert L.lbm_supported(Q, s, m, L.SOA, L.F64)
                 assert L.lbm_supported(Q, s, m, L.AOS, L.F64)
                 assert L.lbm_supported(Q, s, m, L.SOA, L.F32)
                 assert L.lbm_supported(Q, s, m, L.SOA, L.F16)
                 assert not L.lbm_supported(Q, s, m, L.AOS, L.F32)
     assert not L.lbm_supported(21, 0, 0, 0, 0)
-    assert not L.lbm_supported(19, 0, 10, 0, 0)
+    assert not L.lbm_supported(19, 0, 12, 0, 0)

@@ -260,3 +260,17 @@ def test_step_sums_fallback_and_zero_steps():
         g.set_populations(f0)
         g.step(2)
         assert g.reduce() == (m2, e2)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("model", ["BGK_W2_EDU", "BGK_W2_LOOP"])
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_educational_bgk_matches_oracle(Q, model, scheme):
+    """BGK-W2 in the educational form of Section 2.6 (loops over the directions, tabulated c_k
+    and t_k) computes the oracle's BGK-W2 within the FP64 tolerance in every scheme."""
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=181, model="BGK_W2")
+    ref = oracle_run(Q, DIMS, flags, "BGK_W2", p, f0, 5)
+    got = gpu_run(Q, DIMS, flags, model, p, f0, 5, scheme=scheme)
+    assert rel_err(got, ref.f, flags) <= RTOL_F64
+    assert np.all(got[:, flags != 0] == 0.0)

@@ -116,3 +116,15 @@ def test_step_sums_shifted_storage(precision, scheme):
     # the same FP32-stored values agree far closer in practice)
     assert abs(m - m0) <= 1e-7 * m0
     assert abs(e - e0) <= 2e-6 * e0
+
+
+@pytest.mark.parametrize("precision", [L.F32, L.F16])
+@pytest.mark.parametrize("model", ["BGK_W2_EDU", "BGK_W2_LOOP"])
+def test_educational_bgk_shifted_short_run(precision, model):
+    p = prm()
+    flags, f0 = case(19, DIMS, seed=191, model="BGK_W2")
+    ref = oracle_run(19, DIMS, flags, "BGK_W2", p, f0, 6)
+    got = gpu_run(19, DIMS, flags, model, p, f0, 6, scheme="aa", precision=precision)
+    fluid = flags == 0
+    err = np.max(np.abs(got[:, fluid] - ref.f[:, fluid]) / np.abs(ref.f[:, fluid]))
+    assert err <= SHORT_RTOL[precision], err
