@@ -56,6 +56,9 @@ extern "C" {
 #define LBM_API
 #endif
 
+/* largest lattice, nx*ny*nz cells (2^31 - 2^22) */
+#define LBM_MAX_CELLS 2143289344LL
+
 /* ---- status codes ---- */
 #define LBM_OK 0
 #define LBM_ERR_INVALID_ARG (-1) /* bad enum, bad size, NULL pointer, n < 0 */
@@ -111,8 +114,8 @@ extern "C" {
 
 typedef struct lbm_s* lbm_t;
 
-/* Create a lattice.  lattice: 19 or 27; nx, ny, nz >= 1 with N < 2^31;
- * scheme: LBM_TWOPOP..LBM_ESOTWIST; collision: LBM_BGK_W2..LBM_K;
+/* Create a lattice.  lattice: 19 or 27; nx, ny, nz >= 1 with N <= LBM_MAX_CELLS;
+ * scheme: LBM_TWOPOP..LBM_ESOTWIST; collision: LBM_BGK_W2..LBM_BGK_W2_LOOP;
  * omega in (0, 2); flags: host array of N bytes (copied).  Layout SoA and
  * precision FP64 unless changed before the populations are first written.
  * Device memory for the populations is reserved at the first call that

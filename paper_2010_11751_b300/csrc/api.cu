@@ -269,7 +269,9 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
   if (lattice != 19 && lattice != 27) return fail(LBM_ERR_INVALID_ARG, "lattice must be 19 or 27");
   if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_ERR_INVALID_ARG, "dimensions must be >= 1");
   const long long N = (long long)nx * ny * nz;
-  if (N >= (1ll << 31)) return fail(LBM_ERR_INVALID_ARG, "nx*ny*nz must be < 2^31");
+  // cell indices are 32-bit; the headroom keeps one-thread-per-cell indices of
+  // the last block and grid-stride loop indices from overflowing
+  if (N > LBM_MAX_CELLS) return fail(LBM_ERR_INVALID_ARG, "nx*ny*nz must be <= 2^31 - 2^22");
   if (scheme < LBM_TWOPOP || scheme > LBM_ESOTWIST) return fail(LBM_ERR_INVALID_ARG, "unknown scheme");
   if (collision < 0 || collision >= NUM_MODELS) return fail(LBM_ERR_INVALID_ARG, "unknown collision model");
   if (!valid_omega(omega)) return fail(LBM_ERR_INVALID_ARG, "omega must be in (0, 2)");

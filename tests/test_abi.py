@@ -41,6 +41,10 @@ def test_invalid_arguments_rejected(L):
         (19, 3, 3, 3, L.AA, L.TRT, 2.0, fl),            # omega out of (0, 2)
         (19, 3, 3, 3, L.AA, L.TRT, -0.5, fl),
         (19, 3, 3, 3, L.AA, L.TRT, 1.0, np.full(27, 9, np.uint8)),  # flag value > 7
+        # larger than LBM_MAX_CELLS = 2^31 - 2^22 (rejected before the flags are read)
+        (19, 1024, 1024, 2048, L.AA, L.TRT, 1.0, fl),
+        (27, 2047, 1024, 1024, L.AA, L.TRT, 1.0, fl),
+        (19, 1 << 20, 1 << 20, 1 << 20, L.AA, L.TRT, 1.0, fl),  # 2^60 cells: far beyond
     ]
     for args in bad:
         with pytest.raises(L.LBMError) as ei:

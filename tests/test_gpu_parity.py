@@ -274,3 +274,21 @@ def test_educational_bgk_matches_oracle(Q, model, scheme):
     got = gpu_run(Q, DIMS, flags, model, p, f0, 5, scheme=scheme)
     assert rel_err(got, ref.f, flags) <= RTOL_F64
     assert np.all(got[:, flags != 0] == 0.0)
+
+
+def test_out_of_device_memory_is_reported():
+    """A lattice whose populations cannot fit in device memory (D3Q27 FP64, 1200^3 cells:
+    373 GB) is created (flags and masks fit), and the first call that writes populations reports
+    LBM_ERR_OOM without allocating them; the handle stays usable for destroy."""
+    n = 1200
+    flags = np.zeros(n ** 3, np.uint8)
+    g = L.Lattice(27, n, n, n, "aa", "BGK_W2", 1.2, flags)
+    try:
+        with pytest.raises(L.LBMError) as ei:
+            g.init_equilibrium()
+        assert ei.value.code == L.ERR_OOM
+        with pytest.raises(L.LBMError) as ei:
+            g.step(1)  # implicit initialisation: the same pre-flight check
+        assert ei.value.code == L.ERR_OOM
+    finally:
+        g.close()
