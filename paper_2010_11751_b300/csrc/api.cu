@@ -116,6 +116,11 @@ int ensure_nonbulk_list(lbm_s* h) {
   LBM_CUDA(cudaFree(h->d_tile_off));           // only needed to sort the list
   h->d_tile_off = nullptr;
   h->nlist = (int)run;
+  if (run > 0 && !h->side.side) {
+    LBM_CUDA(cudaStreamCreateWithFlags(&h->side.side, cudaStreamNonBlocking));
+    LBM_CUDA(cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming));
+    LBM_CUDA(cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming));
+  }
   return LBM_OK;
 }
 
@@ -444,7 +449,7 @@ int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr
         listed.mask = h->d_list_mask;
         listed.kinds = h->d_list_kinds;
         listed.n = h->nlist;
-        e = h->sfns[odd](a, h->d_err, listed, h->stream);
+        e = h->sfns[odd](a, h->d_err, listed, h->side, h->stream);
       } else {
         e = kernel(odd ? K_AA_ODD : K_AA_EVEN);
       }
@@ -674,6 +679,12 @@ int lbm_destroy(lbm_t h) {
   if (h->d_partials) cudaFree(h->d_partials);
   if (h->d_stage) cudaFree(h->d_stage);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->side.side) {
+    cudaStreamSynchronize(h->side.side);
+    cudaStreamDestroy(h->side.side);
+  }
+  if (h->side.fork) cudaEventDestroy(h->side.fork);
+  if (h->side.join) cudaEventDestroy(h->side.join);
   if (h->d_sum_partials) cudaFree(h->d_sum_partials);
   if (h->d_list) cudaFree(h->d_list);
   if (h->d_tile_off) cudaFree(h->d_tile_off);

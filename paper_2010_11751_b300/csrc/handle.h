@@ -42,6 +42,7 @@ struct lbm_s {
   unsigned long long* d_list_kinds = nullptr;
   int* d_tile_off = nullptr;   // per-tile offsets, only while the list is built
   int nlist = -1;              // number of listed cells; -1 until the list is built
+  lbm::SideStream side;        // for the staged steps' listed-cell kernel
 };
 
 namespace lbm {

@@ -29,9 +29,16 @@ struct Listed {
   const unsigned long long* kinds = nullptr;
   int n = 0;
 };
+// a second stream and two events of a handle, so that a staged step can run
+// its listed-cell kernel beside the staged kernel (side == nullptr: one after
+// the other on the handle's stream)
+struct SideStream {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 // staged AA step: bulk cells through the shared-memory tile pipeline, listed
 // cells from their records; err receives the kernel's error word
-using StagedFn = cudaError_t (*)(const KArgs&, int* err, const Listed& listed, cudaStream_t);
+using StagedFn = cudaError_t (*)(const KArgs&, int* err, const Listed& listed, const SideStream& ss, cudaStream_t);
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);

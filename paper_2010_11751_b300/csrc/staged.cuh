@@ -16,7 +16,8 @@
 // padding past their end.  The staged kernel updates the bulk cells (flag
 // byte 0), reading their populations from shared memory.  The other fluid
 // cells (next to a wall or on a domain face: 1.2 % at 512^3) are updated
-// afterwards by a one-thread-per-cell kernel on the global-memory path, from a
+// by a one-thread-per-cell kernel on the global-memory path, on a second stream
+// beside the staged kernel (the two touch disjoint cells), from a
 // sorted list with a record per cell built once per lattice (solid-neighbour
 // mask, domain-face bit, wall kinds of the solid neighbours), so that each
 // waits on two memory round trips (record, then populations) and reads no
@@ -259,7 +260,8 @@ struct StagedShape {
 // one AA step (SK = K_AA_EVEN or K_AA_ODD) of the whole lattice: the staged
 // kernel over the bulk cells, then the listed-cell kernel
 template <int Q, int M, int P, int SK>
-cudaError_t launch_staged_step(const KArgs& a, int* err, const Listed& listed, cudaStream_t s) {
+cudaError_t launch_staged_step(const KArgs& a, int* err, const Listed& listed, const SideStream& ss,
+                               cudaStream_t s) {
   using Sh = StagedShape<Q>;
   using G = StageLayout<Q, P, Sh::TILE, Sh::STAGES>;
   constexpr int threads = 32 * (1 + Sh::CW);
@@ -275,11 +277,26 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, const Listed& listed, c
   }();
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   const int ntiles = (a.N + Sh::TILE - 1) / Sh::TILE;
+  // the two kernels update disjoint cells: with a side stream, the listed-cell
+  // kernel runs beside the staged kernel (fork after the previous step, join
+  // before the next)
+  const bool side = ss.side && listed.n > 0;
+  cudaError_t e = cudaSuccess;
+  if (side) {
+    e = cudaEventRecord(ss.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.side, ss.fork, 0);
+    if (e != cudaSuccess) return e;
+  }
   if (ntiles > 0) kern<<<ntiles < grid ? ntiles : grid, threads, G::BYTES, s>>>(a, ntiles, err);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess || listed.n <= 0) return e;
-  listed_cells_kernel<Q, M, P, SK><<<(listed.n + 127) / 128, 128, 0, s>>>(a, listed);
-  return cudaGetLastError();
+  listed_cells_kernel<Q, M, P, SK><<<(listed.n + 127) / 128, 128, 0, side ? ss.side : s>>>(a, listed);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && side) {
+    e = cudaEventRecord(ss.join, ss.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss.join, 0);
+  }
+  return e;
 }
 
 // staged AA step of one model, for FP16 storage (SoA); nullptr elsewhere.
