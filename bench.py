@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -82,6 +83,7 @@ def parse():
     ap.add_argument("--matrix", action="store_true", help="also time every scheme x collision x lattice")
     ap.add_argument("--matrix-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None, help="where to keep the raw nvidia-smi samples (default: temp dir)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--forms", default="",
@@ -126,10 +128,11 @@ def workload_name(args):
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
 
-    def __init__(self, index):
+    def __init__(self, index, directory=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples; only their summary goes into the JSON line
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
@@ -222,7 +225,7 @@ def time_native(args, rank, local, pg):
     if pg is not None:
         pg.barrier()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_dir) as clk:
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             evs[0].record(stream)
