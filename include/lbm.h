@@ -137,7 +137,10 @@ LBM_API int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, doubl
  * lambda > 0.  Takes effect at the next step. */
 LBM_API int lbm_set_param(lbm_t h, int key, double value);
 
-/* All device work of this handle goes to this cudaStream_t (NULL: legacy default). */
+/* All device work of this handle goes to this cudaStream_t (NULL: legacy default).
+ * The staged AA steps of FP16 SoA storage also run a kernel on a stream of the
+ * handle's own, forked from and joined back to this one by events, so that
+ * work enqueued here later still follows the whole step. */
 LBM_API int lbm_set_stream(lbm_t h, void* stream);
 
 /* f = the collision model's own equilibrium of (rho, u) on every fluid cell.
