@@ -243,15 +243,25 @@ int lbm::handle_prepare(lbm_s* h) {
   return upload_wall(h);
 }
 
-void lbm::handle_rates(const lbm_s* h, double* omega, double* omc, double* wplus, double* wminus,
-                       double* omega_high, double* trt_minus) {
+void lbm::handle_rates(const lbm_s* h, CP<double>* rd, CP<float>* rf) {
   const KArgs a = make_args(h);
-  *omega = a.omega;
-  *omc = a.omc;
-  *wplus = a.wplus;
-  *wminus = a.wminus;
-  *omega_high = a.omega_high;
-  *trt_minus = a.trt_minus;
+  rd->omega = a.omega;
+  rd->omc = a.omc;
+  rd->wplus = a.wplus;
+  rd->wminus = a.wminus;
+  rd->omega_high = a.omega_high;
+  rd->trt_minus = a.trt_minus;
+  for (int c = 0; c < 4; ++c) {
+    rd->wt[c] = a.wt[c];
+    rd->wt3[c] = a.wt3[c];
+    rd->wm3[c] = a.wm3[c];
+  }
+  rd->hs = a.hs;
+  rd->hd = a.hd;
+  // host conversion rounds to nearest, as the kernels' conversion of their parameters does
+  constexpr int NW = (int)(sizeof(CP<double>) / sizeof(double));
+  for (int w = 0; w < NW; ++w)
+    reinterpret_cast<float*>(rf)[w] = (float)reinterpret_cast<const double*>(rd)[w];
 }
 
 extern "C" {

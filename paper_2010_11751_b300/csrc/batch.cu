@@ -134,7 +134,7 @@ int upload_members(lbm_batch_s* b) {
     d.ny = h->ny;
     d.nz = h->nz;
     d.N = h->N;
-    handle_rates(h, &d.omega, &d.omc, &d.wplus, &d.wminus, &d.omega_high, &d.trt_minus);
+    handle_rates(h, &d.rd, &d.rf);
   }
   if (n > b->cap_members) {
     if (b->d_members) BCUDA(cudaFree(b->d_members));

@@ -22,7 +22,11 @@ struct __align__(16) Member {
   int pad_parity;   // unused
   int block_begin;  // first grid block of the member (within its parity class map)
   int pad0, pad1;
-  double omega, omc, wplus, wminus, omega_high, trt_minus;
+  // the member's relaxation rates in both arithmetic types, derived and rounded
+  // to nearest on the host exactly as a single-lattice kernel rounds its launch
+  // parameters, so that no thread spends FP64 operations or conversions on them
+  CP<double> rd;
+  CP<float> rf;
 };
 
 struct BatchArgs {
@@ -35,9 +39,9 @@ struct BatchArgs {
 // a single body and takes the register bounds of the single-lattice kernels;
 // the host launches it on the members whose step parity matches
 // register bounds of the batch kernels: milder than the single-lattice ones,
-// because the member's pointers, sizes and rates come from a table in global
-// memory and live in registers (a single-lattice kernel reads them from its
-// launch parameters); chosen so that no variant spills
+// because the member's pointers and sizes come from a table in global memory
+// and live in registers (a single-lattice kernel reads them from its launch
+// parameters)
 template <int Q, int M, int P>
 inline constexpr int BATCH_MIN_BLOCKS =
     P == F64 ? 2
@@ -59,29 +63,23 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   a.N = mm->N;
   a.parity = SK == K_AA_ODD ? 1 : 0;
   using R = typename Store<P>::R;
-  CP<R> cp;  // rates converted once per block, in the arithmetic type
-  cp.omega = R(mm->omega);
-  cp.omc = R(mm->omc);
-  cp.wplus = R(mm->wplus);
-  cp.wminus = R(mm->wminus);
-  cp.omega_high = R(mm->omega_high);
-  cp.trt_minus = R(mm->trt_minus);
-  {
-    double wt[4], wt3[4], wm3[4], hs, hd;
-    derived_rates<Q>(mm->omega, mm->trt_minus, wt, wt3, wm3, hs, hd);
-    for (int c = 0; c < 4; ++c) {
-      cp.wt[c] = R(wt[c]);
-      cp.wt3[c] = R(wt3[c]);
-      cp.wm3[c] = R(wm3[c]);
-    }
-    cp.hs = R(hs);
-    cp.hd = R(hd);
+  // the member's rates, staged in shared memory once per block (one word per
+  // thread) and read from there just before each collision
+  constexpr int NW = (int)(sizeof(CP<R>) / sizeof(R));
+  static_assert(sizeof(CP<R>) == NW * sizeof(R), "CP holds rates only");
+  __shared__ CP<R> s_cp;
+  if (threadIdx.x < NW) {
+    const CP<R>* src;
+    if constexpr (std::is_same<R, double>::value) src = &mm->rd;
+    else src = &mm->rf;
+    reinterpret_cast<R*>(&s_cp)[threadIdx.x] = __ldg(reinterpret_cast<const R*>(src) + threadIdx.x);
   }
+  __syncthreads();
   const int base = (blockIdx.x - mm->block_begin) * blockDim.x * b.cpt + threadIdx.x;
 #pragma unroll 1
   for (int j = 0; j < b.cpt; ++j) {
     const int i = base + j * blockDim.x;
-    if (i < a.N) step_one<Q, M, P, SOA, SK>(a, i, [&] { return cp; });
+    if (i < a.N) step_one<Q, M, P, SOA, SK>(a, i, [&] { return s_cp; });
   }
 }
 

@@ -49,7 +49,7 @@ namespace lbm {
 // make a handle ready to be stepped: populations written (rest equilibrium if
 // never written) and the wall table on the device; returns LBM_OK or an error
 int handle_prepare(lbm_s* h);
-// relaxation parameters of the handle, as the step kernels take them
-void handle_rates(const lbm_s* h, double* omega, double* omc, double* wplus, double* wminus, double* omega_high,
-                  double* trt_minus);
+// relaxation rates of the handle in FP64 and rounded to nearest in FP32: the
+// values the step kernels compute with in either arithmetic type
+void handle_rates(const lbm_s* h, CP<double>* rd, CP<float>* rf);
 }  // namespace lbm

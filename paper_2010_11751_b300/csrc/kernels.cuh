@@ -52,8 +52,8 @@ struct KArgs {
   double wt[4], wt3[4], wm3[4], hs, hd;
 };
 
-// rate constants derived from w and w- (host side, and once per block in the
-// batch kernels)
+// rate constants derived from w and w- (on the host: the kernels' launch
+// parameters and the batch member table)
 template <int Q>
 __host__ __device__ inline void derived_rates(double omega, double trt_minus, double (&wt)[4], double (&wt3)[4],
                                               double (&wm3)[4], double& hs, double& hd) {

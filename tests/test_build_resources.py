@@ -1,0 +1,60 @@
+"""Compiler resource report (nvcc -Xptxas -v) of the batch kernels that the serving and batching
+forms run: no stack frame and no spills in FP64 or FP32.
+
+A batch block takes its member's relaxation rates from the member table.  When they ended up in
+per-thread local memory instead of registers or shared memory, every cell's collision re-read
+them from there and the FP64 BGK-W2 batch ran 20 times slower than the same lattice stepped alone,
+while every result stayed bit-identical; only the resource report shows it without a GPU.
+"""
+import os
+import re
+import subprocess
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+from paper_2010_11751_b300 import build as B
+
+F64, F32 = 0, 1
+MODELS = {"model_bgk_w2.cu": 0, "model_k.cu": 9}  # the serving form's collision models
+
+
+def _report(src):
+    with tempfile.TemporaryDirectory() as tmp:
+        cmd = [B._nvcc()] + B.FLAGS + B.ARCH + ["-Xptxas", "-v", "-c", os.path.join(B.CSRC, src),
+                                                "-o", os.path.join(tmp, "x.o")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return r.stderr
+
+
+@pytest.fixture(scope="module")
+def reports():
+    if not os.path.exists(B._nvcc()):
+        pytest.skip("nvcc not available")
+    with ThreadPoolExecutor(len(MODELS)) as ex:
+        return dict(zip(MODELS, ex.map(_report, MODELS)))
+
+
+def _batch_kernels(text):
+    out = []
+    for blk in text.split("Compiling entry function")[1:]:
+        name = blk.split("'")[1]
+        m = re.search(r"batch_aa_kernelILi(\d+)ELi(\d+)ELi(\d+)ELi(\d+)E", name)
+        if not m:
+            continue
+        q, model, prec, sk = map(int, m.groups())
+        frame = int(re.search(r"(\d+) bytes stack frame", blk).group(1))
+        spill = int(re.search(r"(\d+) bytes spill stores", blk).group(1))
+        out.append((q, model, prec, sk, frame, spill))
+    return out
+
+
+@pytest.mark.parametrize("src", sorted(MODELS))
+def test_batch_kernels_keep_rates_out_of_local_memory(reports, src):
+    ks = [k for k in _batch_kernels(reports[src]) if k[2] in (F64, F32)]
+    # D3Q19 and D3Q27, FP64 and FP32, even and odd AA steps
+    assert len(ks) == 8 and {k[1] for k in ks} == {MODELS[src]}, ks
+    bad = [k for k in ks if k[4] or k[5]]
+    assert not bad, f"(Q, model, precision, step kind, stack frame, spill bytes): {bad}"
