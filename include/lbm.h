@@ -236,7 +236,7 @@ LBM_API int lbm_batch_remove(lbm_batch_t b, lbm_t h);
 /* Threads per block (32..256, multiple of 32) and cells per thread (1, 2, 4);
  * 0 selects the defaults (256, 1). */
 LBM_API int lbm_batch_set_launch(lbm_batch_t b, int threads_per_block, int cells_per_thread);
-/* Time every (threads, cells-per-thread) shape in {64,128,256} x {1,2,4}
+/* Time every (threads, cells-per-thread) shape in {32,64,128,256} x {1,2,4}
  * on the batch as it stands (CUDA events on the batch stream) and keep the
  * fastest.  The trial steps advance the members (6 steps per shape).  The
  * choice is cached per (lattice, collision, precision, size class =

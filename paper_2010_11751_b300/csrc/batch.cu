@@ -295,10 +295,10 @@ int lbm_batch_autotune(lbm_batch_t b, int* threads_out, int* cpt_out) {
   BCUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int bt = 256, bc = 1;
-  const int shapes_t[3] = {64, 128, 256};
+  const int shapes_t[4] = {32, 64, 128, 256};
   const int shapes_c[3] = {1, 2, 4};
   int rc = LBM_OK;
-  for (int ti = 0; ti < 3 && rc == LBM_OK; ++ti)
+  for (int ti = 0; ti < 4 && rc == LBM_OK; ++ti)
     for (int ci = 0; ci < 3 && rc == LBM_OK; ++ci) {
       rc = lbm_batch_set_launch(b, shapes_t[ti], shapes_c[ci]);
       if (rc) break;
