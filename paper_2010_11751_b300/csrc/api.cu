@@ -431,6 +431,12 @@ int lbm_init_equilibrium(lbm_t h, const double* rho, const double* u) {
 }
 
 namespace {
+// blocks of the handle's summing step kernel (one pair of partial sums each)
+int sum_blocks(const lbm_s* h) {
+  const long long chunk = (long long)h->threads * sum_cells_per_thread(h->prec);
+  return (int)((h->N + chunk - 1) / chunk);
+}
+
 // enqueue one time step; with sum_partials, the step's kernel also writes the
 // per-block FP64 sums of the state it reads (returns the number of blocks in
 // *nparts), and the caller guarantees that a summing kernel exists
@@ -439,7 +445,7 @@ int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr
   cudaError_t e = cudaSuccess;
   auto kernel = [&](int sk) {
     if (sum_partials) {
-      *nparts = (h->N + h->threads - 1) / h->threads;
+      *nparts = sum_blocks(h);
       return h->sumfns[sk](a, h->threads, sum_partials, h->stream);
     }
     return h->fns[sk](a, h->threads, h->stream);
@@ -526,7 +532,7 @@ int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
     rc = lbm_step(h, n);
     if (rc) return rc;
   } else {
-    const size_t need = 2 * (size_t)((h->N + h->threads - 1) / h->threads);
+    const size_t need = 2 * (size_t)sum_blocks(h);
     if (h->sum_partials_cap < need) {
       if (h->d_sum_partials) {
         LBM_CUDA(cudaStreamSynchronize(h->stream));

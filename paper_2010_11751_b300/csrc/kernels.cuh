@@ -392,15 +392,34 @@ using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
 
 using StepSumFn = cudaError_t (*)(const KArgs&, int threads, double* partials, cudaStream_t);
 
+// cells per thread of the summing step kernels.  With FP64 arithmetic the
+// kernel is bound by the FP64 pipe, and every lane of the warp's shuffle tree
+// adds (5 levels x 2 sums = 10 operations per thread), so four cells share one
+// tree; the memory-bound FP32 and FP16 kernels keep one cell per thread.
+__host__ __device__ constexpr int sum_cells_per_thread(int P) { return P == F64 ? 4 : 1; }
+
 // a step kernel that also sums, over its block, the FP64 mass and kinetic
 // energy of the fluid cells it reads (the collision's own moments), and writes
-// them to partials[2 * block], partials[2 * block + 1] in a fixed order
+// them to partials[2 * block], partials[2 * block + 1] in a fixed order; a
+// block covers sum_cells_per_thread(P) x blockDim.x consecutive cells
 template <int Q, int M, int P, int L, int SK>
 __global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_sum_kernel(KArgs a, double* partials) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  CellSums cs{0.0, 0.0};
-  if (i < a.N) step_one<Q, M, P, L, SK>(a, i, [&] { return rates<P>(a); }, &cs);
-  double m = cs.rho, e = cs.ke;
+  constexpr int CPT = sum_cells_per_thread(P);
+  const int base = blockIdx.x * blockDim.x * CPT + threadIdx.x;
+  double m = 0.0, e = 0.0;
+#pragma unroll 1
+  for (int j = 0; j < CPT; ++j) {
+    const int i = base + j * (int)blockDim.x;
+    CellSums cs{0.0, 0.0};
+    if (i < a.N) step_one<Q, M, P, L, SK>(a, i, [&] { return rates<P>(a); }, &cs);
+    if (j == 0) {
+      m = cs.rho;
+      e = cs.ke;
+    } else {
+      m += cs.rho;
+      e += cs.ke;
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) {
     m += __shfl_down_sync(0xffffffffu, m, o);
     e += __shfl_down_sync(0xffffffffu, e, o);
@@ -425,7 +444,8 @@ __global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_sum_kernel(KArg
 
 template <int Q, int M, int P, int L, int SK>
 cudaError_t launch_step_sum(const KArgs& a, int threads, double* partials, cudaStream_t s) {
-  const int blocks = (a.N + threads - 1) / threads;
+  const long long chunk = (long long)threads * sum_cells_per_thread(P);
+  const int blocks = (int)((a.N + chunk - 1) / chunk);
   step_sum_kernel<Q, M, P, L, SK><<<blocks, threads, 0, s>>>(a, partials);
   return cudaGetLastError();
 }
