@@ -35,9 +35,6 @@ struct BatchArgs {
   int cpt;                  // cells per thread
 };
 
-// one kernel per AA step kind (SK = K_AA_EVEN or K_AA_ODD), so that each holds
-// a single body and takes the register bounds of the single-lattice kernels;
-// the host launches it on the members whose step parity matches
 // register bounds of the batch kernels: milder than the single-lattice ones,
 // because the member's pointers and sizes come from a table in global memory
 // and live in registers (a single-lattice kernel reads them from its launch
@@ -47,6 +44,8 @@ inline constexpr int BATCH_MIN_BLOCKS =
     P == F64 ? 2
              : (MIN_BLOCKS<Q, M, P> == 1 ? 1 : (Q == 19 ? 4 : 3));
 
+// one kernel per AA step kind (SK = K_AA_EVEN or K_AA_ODD), so that each holds
+// a single body; the host launches it on the members whose step parity matches
 template <int Q, int M, int P, int SK>
 __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kernel(BatchArgs b) {
   const int mi = __ldg(b.block_member + blockIdx.x);
