@@ -1,5 +1,6 @@
-"""Compiler resource report (nvcc -Xptxas -v) of the batch kernels that the serving and batching
-forms run: no stack frame and no spills in FP64 or FP32.
+"""Compiler resource report (nvcc -Xptxas -v) of the kernels of BGK-W2 and the cumulant model: no
+stack frame and no spills in the FP64 and FP32 batch kernels (the serving mix) or in the FP64
+single-lattice and summing step kernels (the headline step and lbm_step_sums).
 
 A batch block takes its member's relaxation rates from the member table.  When they ended up in
 per-thread local memory instead of registers or shared memory, every cell's collision re-read
@@ -58,3 +59,29 @@ def test_batch_kernels_keep_rates_out_of_local_memory(reports, src):
     assert len(ks) == 8 and {k[1] for k in ks} == {MODELS[src]}, ks
     bad = [k for k in ks if k[4] or k[5]]
     assert not bad, f"(Q, model, precision, step kind, stack frame, spill bytes): {bad}"
+
+
+def _step_kernels(text):
+    out = []
+    for blk in text.split("Compiling entry function")[1:]:
+        name = blk.split("'")[1]
+        m = re.search(r"(step_kernel|step_sum_kernel)ILi(\d+)ELi(\d+)ELi(\d+)ELi(\d+)ELi(\d+)E", name)
+        if not m:
+            continue
+        q, model, prec, layout, sk = map(int, m.groups()[1:])
+        frame = int(re.search(r"(\d+) bytes stack frame", blk).group(1))
+        spill = int(re.search(r"(\d+) bytes spill stores", blk).group(1))
+        out.append((m.group(1), q, model, prec, layout, sk, frame, spill))
+    return out
+
+
+@pytest.mark.parametrize("src", sorted(MODELS))
+def test_fp64_step_kernels_keep_everything_in_registers(reports, src):
+    """The FP64 single-lattice and summing step kernels (the headline step and the first step of
+    lbm_step_sums) are bound by the FP64 pipe; local-memory traffic would come on top of it."""
+    ks = [k for k in _step_kernels(reports[src]) if k[3] == F64]
+    # step kernels: D3Q19/D3Q27 x SoA/AoS x 4 step kinds; summing kernels: SoA only
+    assert len([k for k in ks if k[0] == "step_kernel"]) == 16, ks
+    assert len([k for k in ks if k[0] == "step_sum_kernel"]) == 8, ks
+    bad = [k for k in ks if k[6] or k[7]]
+    assert not bad, f"(kernel, Q, model, precision, layout, step kind, stack frame, spill bytes): {bad}"
