@@ -269,3 +269,61 @@ def test_cumulant_relaxation_law(Q):
         K, Ks = O.cumulants(Q, f), O.cumulants(Q, fo)
         Keq = np.array([CS2 if (sorted(e) == [0, 0, 2]) else 0.0 for e in pqr])
         _check_relaxation(Q, K, Ks, Keq, pqr, w, wb, wh)
+
+
+def _rr_expected_high(pqr, u, n2):
+    """Order >= 3 Hermite moments the recursive regularization prescribes, by a route of
+    its own: each is m(u) + 1/2 sum_ab n2_ab d^2 m / du_a du_b with m(u) = ux^p uy^q uz^r.
+    The second derivative picks every unordered pair of the moment's index multiset once
+    (p_a p_b pairs for a != b, p_a (p_a - 1)/2 for a = b), so this is the sum over index
+    pairs of n2_pair times the product of the remaining velocities, with the pair counts
+    supplied by calculus rather than by an enumeration of indices."""
+    us = sp.symbols("ux uy uz")
+    sub = dict(zip(us, [float(v) for v in u]))
+    out = {}
+    for j, (p, q, r) in enumerate(pqr):
+        if p + q + r < 3:
+            continue
+        m = us[0] ** int(p) * us[1] ** int(q) * us[2] ** int(r)
+        corr = sum(sp.Rational(1, 2) * n2[a][b] * sp.diff(m, us[a], us[b]) for a in range(3) for b in range(3))
+        out[j] = float((m + corr).subs(sub))
+    return out
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_rr_recursive_high_order_moments(Q):
+    """RR (recursive regularization, Section 2.2 list of models; moment route of Section 2.6):
+    at u ~ 0.1 and omega != 1, with the bulk coupling on and omega_high != 1 (which RR
+    ignores), the post-collision Hermite moments computed here from f_out satisfy
+      * second order: the relaxation law with the bulk coupling;
+      * order >= 3: X*_j = prod u + sum over index pairs of neq2*_pair prod(remaining u),
+        where neq2* = X*_2 - prod u is the post-collision second-order non-equilibrium.
+    A dropped pair, a swapped axis or a u written for a neq2 term moves an order-3 moment
+    by ~1e-3 and an order-6 one by ~1e-7, both far above the 1e-15 tolerance."""
+    c, t, _ = O.lattice(Q)
+    T, pqr = _moment_matrix(Q, hermite=True)
+    w, wb, wh = 1.6, 1.1, 0.7
+    for s in range(4):
+        g = np.random.default_rng(1200 + s)
+        u0 = np.array([0.11, -0.08, 0.06]) * (1.0 + 0.3 * g.uniform(-1, 1, 3))
+        f = O.equilibrium(Q, 0, 1.0 + 0.05 * g.standard_normal(), u0) * (1.0 + 0.04 * g.standard_normal(Q))
+        rho, u = _rho_u(Q, f)
+        assert np.abs(u).min() > 0.03  # the recursive terms are not negligible here
+        fo = O.collide(Q, "RR", O.params(w, wb, wh), f)
+        X, Xs = T @ f / rho, T @ fo / rho
+        Xeq = np.array([u[0] ** a * u[1] ** b * u[2] ** gg for a, b, gg in pqr])
+        _check_relaxation(Q, X, Xs, Xeq, pqr, w, wb, wh, skip_high=True)
+        n2 = [[0.0] * 3 for _ in range(3)]
+        for a in range(3):
+            for b in range(3):
+                e = [0, 0, 0]
+                e[a] += 1
+                e[b] += 1
+                j = int(np.where((pqr == np.array(e)).all(1))[0][0])
+                n2[a][b] = Xs[j] - Xeq[j]
+        want = _rr_expected_high(pqr, u, n2)
+        assert len(want) == (9 if Q == 19 else 17)  # D3Q19: 6 of order 3, 3 of order 4
+        for j, v in want.items():
+            assert abs(Xs[j] - v) < 1e-15, (tuple(pqr[j]), Xs[j], v)
+            # the recursive part is exercised far above the tolerance (order 3: ~1e-3)
+            assert abs(v - Xeq[j]) > 1e-9

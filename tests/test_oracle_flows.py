@@ -160,3 +160,33 @@ def test_streaming_brute_force(Q, dims):
     lat.f = f.copy()
     lat.step(1)
     assert np.array_equal(lat.f, _pull_by_hand(Q, nx, ny, nz, flags, lat.wall_u, f))
+
+
+@pytest.mark.parametrize("Q,model", [(19, "BGK_W2"), (27, "BGK_NW4"), (19, "K")])
+def test_conserved_sums_of_known_fields(Q, model):
+    """The oracle's FP64 sums against their definitions (fluid cells only):
+    mass = sum rho and energy = sum rho |u|^2 / 2.  A uniform flow of known rho and u gives
+    N_fluid rho and N_fluid rho |u|^2 / 2; a smooth random field gives the same sums formed
+    here in numpy from the (rho, u) it was built from, since every model's equilibrium
+    reproduces its own rho and u."""
+    nx, ny, nz = 6, 5, 4
+    N = nx * ny * nz
+    flags = np.zeros(N, np.uint8)
+    flags[[3, 17, 60, 99]] = [1, 2, 1, 3]
+    fluid = flags == 0
+    rho0, u0 = 1.03, np.array([0.03, -0.02, 0.011])
+    lat = O.Lattice(Q, nx, ny, nz, flags, model, O.params(1.2))
+    lat.init_equilibrium(np.full(N, rho0), np.repeat(u0[:, None], N, axis=1))
+    m, e = lat.conserved()
+    nf = int(fluid.sum())
+    assert abs(m - nf * rho0) <= 1e-14 * nf
+    assert abs(e - nf * 0.5 * rho0 * float(u0 @ u0)) <= 1e-12 * nf * 0.5 * rho0 * float(u0 @ u0)
+    g = np.random.default_rng(31)
+    rho = 1.0 + 0.02 * g.standard_normal(N)
+    u = 0.04 * g.standard_normal((3, N))
+    lat.init_equilibrium(rho, u)
+    m, e = lat.conserved()
+    want_m = rho[fluid].sum()
+    want_e = (0.5 * rho * (u * u).sum(0))[fluid].sum()
+    assert abs(m - want_m) <= 1e-13 * want_m
+    assert abs(e - want_e) <= 1e-12 * want_e
