@@ -111,6 +111,15 @@ extern "C" {
 #define LBM_PARAM_OMEGA_BULK 1 /* omega_nu_b of the bulk coupling; default: follows omega */
 #define LBM_PARAM_OMEGA_HIGH 2 /* rate of moments of order >= 3; default 1 */
 #define LBM_PARAM_TRT_LAMBDA 3 /* TRT magic parameter; default 1/4 */
+/* Bound, in SM clock cycles, of each wait in the copy pipeline of the staged
+ * AA steps (FP16 SoA storage; see lbm_step); default 2^32, about 2 s at
+ * 2 GHz.  Integer values in [1, 2^40].  A bound far below a copy's latency
+ * (a few hundred cycles) makes the waits give up, which is how the
+ * LBM_ERR_TIMEOUT path is exercised: the step's results are then undefined and
+ * the handle reports LBM_ERR_TIMEOUT from then on.  Before a block of the
+ * staged kernel exits, it always waits for its own copies in flight with the
+ * default bound, whatever this value is. */
+#define LBM_PARAM_WAIT_CYCLES 4
 
 typedef struct lbm_s* lbm_t;
 
@@ -134,7 +143,8 @@ LBM_API int lbm_set_precision(lbm_t h, int precision);
 LBM_API int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, double uz);
 
 /* Set LBM_PARAM_*.  omega and omega_bulk in (0, 2), omega_high in (0, 2],
- * lambda > 0.  Takes effect at the next step. */
+ * lambda > 0, wait_cycles an integer in [1, 2^40].  Takes effect at the next
+ * step. */
 LBM_API int lbm_set_param(lbm_t h, int key, double value);
 
 /* All device work of this handle goes to this cudaStream_t (NULL: legacy default).
@@ -265,17 +275,21 @@ LBM_API int lbm_batch_destroy(lbm_batch_t b);
  *   [Q][N].  flags: device pointer, one byte per cell, 0 = fluid, 1..7 =
  *   solid (solid cells are skipped).  out: device pointer to 2 doubles,
  *   receives {sum rho, sum rho |u|^2 / 2} over fluid cells.  stream: a
- *   cudaStream_t or NULL.  Asynchronous: out is written when the stream
- *   reaches the kernels.
+ *   cudaStream_t of the current device, or NULL.  Asynchronous: out is
+ *   written when the stream reaches the kernels.
  * Scratch: a 256 KiB array in device global memory, fixed in the library
  * image, which every GPU that loads the library keeps until the process
  * exits.  Its address is looked up (cudaGetSymbolAddress) on the first call
- * made on each device, with that device current; make that first call before
- * any stream capture.  All calls share the array: calls whose kernels overlap
- * on the GPU (different streams, or concurrent host threads) race and must
- * be serialised by the caller.  No cudaMalloc, cudaFree or allocating
- * routine is called.  Non-device pointers are rejected with
- * LBM_ERR_INVALID_ARG before any kernel runs. */
+ * made in each device context, with that device current, and kept for that
+ * context (keyed by the context's unique id, so that a context made again
+ * after cudaDeviceReset is looked up afresh); make the first call on a device
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU (different streams, or concurrent host threads) race
+ * and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating routine is called.  Pointers that are not device memory of the
+ * current device (or managed memory), and a stream of another device, are
+ * rejected with LBM_ERR_INVALID_ARG before any kernel runs; the sizes of the
+ * buffers cannot be checked here and are the caller's to get right. */
 LBM_API int lbm_conserved_sums_static(int lattice, int N, const double* f, const uint8_t* flags, double* out,
                                       void* stream);
 

@@ -398,6 +398,11 @@ int lbm_set_param(lbm_t h, int key, double v) {
       if (!(std::isfinite(v) && v > 0.0)) return fail(LBM_ERR_INVALID_ARG, "lambda must be > 0");
       h->lambda = v;
       return LBM_OK;
+    case LBM_PARAM_WAIT_CYCLES:
+      if (!(std::isfinite(v) && v >= 1.0 && v <= 1099511627776.0))
+        return fail(LBM_ERR_INVALID_ARG, "wait_cycles must be in [1, 2^40]");
+      h->wait_cycles = (long long)v;
+      return LBM_OK;
     default:
       return fail(LBM_ERR_INVALID_ARG, "unknown parameter key");
   }
@@ -465,7 +470,7 @@ int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr
         listed.mask = h->d_list_mask;
         listed.kinds = h->d_list_kinds;
         listed.n = h->nlist;
-        e = h->sfns[odd](a, h->d_err, listed, h->side, h->stream);
+        e = h->sfns[odd](a, h->d_err, h->wait_cycles, listed, h->side, h->stream);
       } else {
         e = kernel(odd ? K_AA_ODD : K_AA_EVEN);
       }

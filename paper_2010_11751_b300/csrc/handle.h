@@ -36,6 +36,7 @@ struct lbm_s {
   double* d_sum_partials = nullptr;                 // their per-block partial sums
   size_t sum_partials_cap = 0;                      // doubles allocated there
   int* d_err = nullptr;        // [0] error word of the staged kernels, [1] scratch counter
+  long long wait_cycles = 1LL << 32;  // bound of each staged-pipeline wait (SM clock cycles)
   // fluid cells with a non-zero flag byte (staged steps), sorted, and their records
   int* d_list = nullptr;
   uint32_t* d_list_mask = nullptr;

@@ -38,7 +38,9 @@ struct SideStream {
 };
 // staged AA step: bulk cells through the shared-memory tile pipeline, listed
 // cells from their records; err receives the kernel's error word
-using StagedFn = cudaError_t (*)(const KArgs&, int* err, const Listed& listed, const SideStream& ss, cudaStream_t);
+// and wait_cycles bounds each wait of its copy pipeline (SM clock cycles)
+using StagedFn = cudaError_t (*)(const KArgs&, int* err, long long wait_cycles, const Listed& listed,
+                                 const SideStream& ss, cudaStream_t);
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);

@@ -38,9 +38,14 @@
 // `empty` barrier (one arrival per consumer warp once it has read the stage),
 // so no block-wide barrier is taken inside the tile loop.
 //
-// Every wait on an mbarrier is bounded in time; on a timeout the thread
-// records an error code in *err and leaves the loop; the producer first waits
-// (bounded) for its own copies still in flight.
+// Every wait of the pipeline (consumers on `full`, the producer on `empty`) is
+// bounded by `wait_cycles` SM clock cycles (set by the host; about 2 s unless
+// changed); on a timeout the thread records an error code in *err and leaves
+// the loop.  Whether its loop ended normally or on a timeout, the producer
+// then waits (bounded by the default ~2 s, whatever wait_cycles is) until the
+// copies of the last STAGES stages it issued have landed, so that no block
+// exits while a bulk copy is still writing into its shared memory -- even
+// when its consumer warps gave up early.
 #pragma once
 #include "internal.h"
 #include "kernels.cuh"
@@ -70,11 +75,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
-// wait for the phase with parity `phase` to complete; false after ~2 s
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+// default bound of a wait, in SM clock cycles (about 2 s at 2 GHz)
+constexpr long long WAIT_CYCLES_DEFAULT = 1LL << 32;
+// wait for the phase with parity `phase` to complete; false once `bound`
+// cycles have passed without it
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
+                                                  long long bound = WAIT_CYCLES_DEFAULT) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, phase))
-    if (clock64() - t0 > (1LL << 32)) return false;
+    if (clock64() - t0 > bound) return false;
   return true;
 }
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -166,7 +175,7 @@ inline constexpr int STAGED_MIN_BLOCKS = (M == BGK_W2 || M == TRT || M == REG) ?
 // one producer warp and CW consumer warps per block
 template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW>
 __global__ void __launch_bounds__(32 * (1 + CW), STAGED_MIN_BLOCKS<Q, M, P>)
-    staged_aa_kernel(KArgs a, int ntiles, int* err) {
+    staged_aa_kernel(KArgs a, int ntiles, int* err, long long wait_cycles) {
   using G = StageLayout<Q, P, TILE, STAGES>;
   using R = typename Store<P>::R;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -180,24 +189,30 @@ __global__ void __launch_bounds__(32 * (1 + CW), STAGED_MIN_BLOCKS<Q, M, P>)
   }
   __syncthreads();
   if (warp == 0) {
-    // producer
+    // producer; `it` counts the stages issued
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int st = it % STAGES;
       if (it >= STAGES) {
         // wait until every consumer warp has released the previous use of st
+        // (the whole warp takes one decision, so that no lane issues a copy
+        // after the others have stopped)
         const uint32_t ph = (uint32_t)((it / STAGES - 1) & 1);
-        if (!mbar_wait_bounded(smem_addr(smem + 8 * (STAGES + st)), ph)) {
-          if (lane == 0) {
-            atomicOr(err, STAGE_ERR_TIMEOUT);
-            // copies of the stages issued before this one may still be in flight
-            for (int j = it - STAGES + 1; j < it; ++j)
-              mbar_wait_bounded(smem_addr(smem + 8 * (j % STAGES)), (uint32_t)((j / STAGES) & 1));
-          }
-          return;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(smem + 8 * (STAGES + st)), ph, wait_cycles))) {
+          if (lane == 0) atomicOr(err, STAGE_ERR_TIMEOUT);
+          break;
         }
       }
       stage_issue_lane<Q, P, SK, TILE, STAGES>(a, smem, tile, st, lane);
+    }
+    // drain: stage j (of the last STAGES issued) has had one use since its
+    // previous release, so its `full` phase of parity (j / STAGES) & 1 is the
+    // one that completes when stage j's copies have landed (already complete
+    // when the consumers took it)
+    if (lane == 0) {
+      for (int j = it > STAGES ? it - STAGES : 0; j < it; ++j)
+        if (!mbar_wait_bounded(smem_addr(smem + 8 * (j % STAGES)), (uint32_t)((j / STAGES) & 1)))
+          atomicOr(err, STAGE_ERR_TIMEOUT);
     }
     return;
   }
@@ -208,7 +223,9 @@ __global__ void __launch_bounds__(32 * (1 + CW), STAGED_MIN_BLOCKS<Q, M, P>)
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int st = it % STAGES;
     const uint32_t full = smem_addr(smem + 8 * st);
-    if (!mbar_wait_bounded(full, (uint32_t)((it / STAGES) & 1))) {
+    // one decision per warp: a warp leaves whole, never with some lanes still
+    // due at the __syncwarp below
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(full, (uint32_t)((it / STAGES) & 1), wait_cycles))) {
       if (lane == 0) atomicOr(err, STAGE_ERR_TIMEOUT);
       return;
     }
@@ -260,8 +277,8 @@ struct StagedShape {
 // one AA step (SK = K_AA_EVEN or K_AA_ODD) of the whole lattice: the staged
 // kernel over the bulk cells, then the listed-cell kernel
 template <int Q, int M, int P, int SK>
-cudaError_t launch_staged_step(const KArgs& a, int* err, const Listed& listed, const SideStream& ss,
-                               cudaStream_t s) {
+cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, const Listed& listed,
+                               const SideStream& ss, cudaStream_t s) {
   using Sh = StagedShape<Q>;
   using G = StageLayout<Q, P, Sh::TILE, Sh::STAGES>;
   constexpr int threads = 32 * (1 + Sh::CW);
@@ -287,7 +304,7 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, const Listed& listed, c
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.side, ss.fork, 0);
     if (e != cudaSuccess) return e;
   }
-  if (ntiles > 0) kern<<<ntiles < grid ? ntiles : grid, threads, G::BYTES, s>>>(a, ntiles, err);
+  if (ntiles > 0) kern<<<ntiles < grid ? ntiles : grid, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles);
   e = cudaGetLastError();
   if (e != cudaSuccess || listed.n <= 0) return e;
   listed_cells_kernel<Q, M, P, SK><<<(listed.n + 127) / 128, 128, 0, side ? ss.side : s>>>(a, listed);

@@ -9,6 +9,7 @@
 // The caller passes the populations, the flags and the output; the per-block
 // partial sums go to the fixed array below, which every GPU that loads the
 // library holds until the process exits.
+#include <cuda.h>  // driver types only: the two driver calls below are reached through the runtime
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -106,34 +107,79 @@ __global__ void static_final_kernel(const double* __restrict__ partials, int nb,
   }
 }
 
-// device address of the scratch array, looked up once per device
-std::mutex g_static_mu;
-double* g_static_addr[SR_MAX_DEVICES] = {};
+// Device address of the scratch array, looked up once per device context.
+// The key is the current context's unique id (cuCtxGetId), not the device
+// index alone: after cudaDeviceReset the device's next primary context loads
+// the library's device code again, at another address, and gets a new id.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+std::once_flag g_driver_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
-int static_scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+void load_driver_entry_points() {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+  fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(fn);
+  cudaGetLastError();
+}
+
+// unique id of the calling thread's current context; false if there is none
+// or it cannot be had (then nothing is cached and every call looks up)
+bool current_context_id(unsigned long long* id) {
+  std::call_once(g_driver_once, load_driver_entry_points);
+  if (!g_ctx_get_current || !g_ctx_get_id) return false;
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+struct ScratchEntry {
+  unsigned long long ctx_id = 0;
+  double* addr = nullptr;
+};
+std::mutex g_static_mu;
+ScratchEntry g_static_addr[SR_MAX_DEVICES];
+
+int static_scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= SR_MAX_DEVICES) return lbm::set_error(LBM_ERR_INVALID_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_partials);
-    if (e != cudaSuccess || !p)
-      return lbm::set_error(LBM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch array failed");
-    g_static_addr[dev] = static_cast<double*>(p);
+  unsigned long long id = 0;
+  ScratchEntry& c = g_static_addr[dev];
+  if (c.addr && current_context_id(&id) && id == c.ctx_id) {
+    *out = c.addr;
+    return LBM_OK;
   }
-  *out = g_static_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+  if (e != cudaSuccess || !p)
+    return lbm::set_error(LBM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch array failed");
+  // the lookup made the device's context current if it was not yet
+  if (current_context_id(&id)) {
+    c.ctx_id = id;
+    c.addr = static_cast<double*>(p);
+  } else {
+    c = ScratchEntry{};
+  }
+  *out = static_cast<double*>(p);
   return LBM_OK;
 }
 
-bool device_accessible(const void* p) {
+// device memory of device `dev`, or managed memory
+bool device_accessible(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -146,17 +192,28 @@ extern "C" LBM_API int lbm_conserved_sums_static(int lattice, int N, const doubl
     return lbm::set_error(LBM_ERR_INVALID_ARG,
                           "N must be in [1, 33554432]: the fixed scratch holds partial sums for 16384 blocks "
                           "of 2048 cells");
-  if (!device_accessible(f) || !device_accessible(flags) || !device_accessible(out))
-    return lbm::set_error(LBM_ERR_INVALID_ARG, "f, flags and out must be device (or managed) pointers");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+  if (!device_accessible(f, dev) || !device_accessible(flags, dev) || !device_accessible(out, dev))
+    return lbm::set_error(LBM_ERR_INVALID_ARG,
+                          "f, flags and out must be device memory of the current device (or managed memory)");
+  cudaStream_t s = (cudaStream_t)stream;
+  int sdev = -1;
+  e = cudaStreamGetDevice(s, &sdev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return lbm::set_error(LBM_ERR_INVALID_ARG, "stream is not a valid CUDA stream");
+  }
+  if (sdev != dev) return lbm::set_error(LBM_ERR_INVALID_ARG, "stream belongs to another device than the current one");
   double* partials = nullptr;
-  int rc = static_scratch_address(&partials);
+  int rc = static_scratch_address(dev, &partials);
   if (rc != LBM_OK) return rc;
   const int nb = (N + SR_CELLS_PER_BLOCK - 1) / SR_CELLS_PER_BLOCK;
-  cudaStream_t s = (cudaStream_t)stream;
   if (lattice == 19) static_partials_kernel<19><<<nb, SR_THREADS, 0, s>>>(f, flags, N, partials);
   else static_partials_kernel<27><<<nb, SR_THREADS, 0, s>>>(f, flags, N, partials);
   static_final_kernel<<<1, 1024, 0, s>>>(partials, nb, out);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }

@@ -27,7 +27,7 @@ MODELS = {"BGK_W2": BGK_W2, "BGK_NW4": BGK_NW4, "TRT": TRT, "REG": REG, "RR": RR
 SOA, AOS = 0, 1
 F64, F32, F16 = 0, 1, 2
 PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}
-PARAM_OMEGA, PARAM_OMEGA_BULK, PARAM_OMEGA_HIGH, PARAM_TRT_LAMBDA = 0, 1, 2, 3
+PARAM_OMEGA, PARAM_OMEGA_BULK, PARAM_OMEGA_HIGH, PARAM_TRT_LAMBDA, PARAM_WAIT_CYCLES = 0, 1, 2, 3, 4
 
 
 class LBMError(RuntimeError):
@@ -206,9 +206,29 @@ def lbm_supported(lattice, scheme, collision, layout, precision):
     return bool(lib().lbm_supported(lattice, scheme, collision, layout, precision))
 
 
+def _check_static_buffers(lattice, N, f, flags, out):
+    """Sizes, types and device of torch tensors handed to lbm_conserved_sums_static (the C
+    side sees bare pointers and cannot check sizes)."""
+    if not 1 <= int(N) <= 33554432:
+        return  # the C call rejects the size itself, with its limit in the message
+    want = (("f", f, "float64", lattice * int(N)), ("flags", flags, "uint8", int(N)), ("out", out, "float64", 2))
+    for name, t, dtype, numel in want:
+        if not hasattr(t, "data_ptr"):
+            continue
+        if str(t.dtype) != "torch." + dtype:
+            raise LBMError(ERR_INVALID_ARG, f"{name} must be a {dtype} tensor, got {t.dtype}")
+        if t.numel() < numel:
+            raise LBMError(ERR_INVALID_ARG, f"{name} holds {t.numel()} elements, needs {numel}")
+        if t.device.type == "cuda":
+            import torch
+            if t.device.index != torch.cuda.current_device():
+                raise LBMError(ERR_INVALID_ARG, f"{name} is on {t.device}, not the current device")
+
+
 def lbm_conserved_sums_static(lattice, N, f, flags, out, stream=None):
     """FP64 {sum rho, sum rho|u|^2/2} of canonical device populations into device out[2];
     allocates nothing (fixed library scratch; see include/lbm.h)."""
+    _check_static_buffers(lattice, N, f, flags, out)
     return _check(lib().lbm_conserved_sums_static(lattice, N, ptr(f), ptr(flags), ptr(out), stream))
 
 

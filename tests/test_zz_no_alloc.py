@@ -90,3 +90,40 @@ def test_rejects_sizes_and_host_pointers_without_launching():
         L.lbm_conserved_sums_static(Q, 64, host_f, flags_dev, out)
     assert ei.value.code == L.ERR_INVALID_ARG
     torch.cuda.synchronize()
+
+
+def test_rejects_wrong_dtype_and_short_buffers():
+    """Bad buffers are refused before the C call can launch anything: a float32 f, an f or
+    out with too few elements, and flags of the wrong type."""
+    torch = pytest.importorskip("torch")
+    Q, N = 19, 64
+    f_dev = torch.zeros(Q * N, dtype=torch.float64, device="cuda")
+    flags_dev = torch.zeros(N, dtype=torch.uint8, device="cuda")
+    out = torch.full((2,), -7.0, dtype=torch.float64, device="cuda")
+    bad = [(f_dev.float(), flags_dev, out), (f_dev[: Q * N - 1], flags_dev, out), (f_dev, flags_dev.int(), out),
+           (f_dev, flags_dev[: N - 3], out), (f_dev, flags_dev, out[:1])]
+    for f, fl, o in bad:
+        with pytest.raises(L.LBMError) as ei:
+            L.lbm_conserved_sums_static(Q, N, f, fl, o)
+        assert ei.value.code == L.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert out.tolist() == [-7.0, -7.0]  # nothing was launched
+
+
+def test_no_device_memory_is_taken():
+    """After a first call (which may load the library's device code), further calls leave
+    the device's free memory unchanged: the scratch is the library's fixed array."""
+    torch = pytest.importorskip("torch")
+    Q, N = 27, 40000
+    f_dev = torch.rand(Q * N, dtype=torch.float64, device="cuda") + 0.01
+    flags_dev = torch.zeros(N, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    L.lbm_conserved_sums_static(Q, N, f_dev, flags_dev, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        L.lbm_conserved_sums_static(Q, N, f_dev, flags_dev, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert abs(out[0].item() - f_dev.sum().item()) <= 1e-12 * f_dev.sum().item()
