@@ -193,8 +193,13 @@ KArgs make_args(const lbm_s* h) {
   a.wplus = a.wminus + w;
   a.omega_high = h->omega_high;
   a.trt_minus = 1.0 / (0.5 + h->lambda / (1.0 / w - 0.5));
-  if (h->Q == 19) derived_rates<19>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
-  else derived_rates<27>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+  if (h->Q == 19) {
+    derived_rates<19>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+    a.dk = derived_dfk<19>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+  } else {
+    derived_rates<27>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+    a.dk = derived_dfk<27>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+  }
   return a;
 }
 
@@ -258,10 +263,22 @@ void lbm::handle_rates(const lbm_s* h, CP<double>* rd, CP<float>* rf) {
   }
   rd->hs = a.hs;
   rd->hd = a.hd;
+  rd->dk = a.dk;
   // host conversion rounds to nearest, as the kernels' conversion of their parameters does
-  constexpr int NW = (int)(sizeof(CP<double>) / sizeof(double));
-  for (int w = 0; w < NW; ++w)
-    reinterpret_cast<float*>(rf)[w] = (float)reinterpret_cast<const double*>(rd)[w];
+  rf->omega = (float)rd->omega;
+  rf->omc = (float)rd->omc;
+  rf->wplus = (float)rd->wplus;
+  rf->wminus = (float)rd->wminus;
+  rf->omega_high = (float)rd->omega_high;
+  rf->trt_minus = (float)rd->trt_minus;
+  for (int c = 0; c < 4; ++c) {
+    rf->wt[c] = (float)rd->wt[c];
+    rf->wt3[c] = (float)rd->wt3[c];
+    rf->wm3[c] = (float)rd->wm3[c];
+  }
+  rf->hs = (float)rd->hs;
+  rf->hd = (float)rd->hd;
+  rf->dk = rd->dk;
 }
 
 extern "C" {

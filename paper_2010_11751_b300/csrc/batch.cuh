@@ -62,16 +62,17 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   a.N = mm->N;
   a.parity = SK == K_AA_ODD ? 1 : 0;
   using R = typename Store<P>::R;
-  // the member's rates, staged in shared memory once per block (one word per
-  // thread) and read from there just before each collision
+  // the member's rates, staged in shared memory once per block and read
+  // from there just before each collision
   constexpr int NW = (int)(sizeof(CP<R>) / sizeof(R));
   static_assert(sizeof(CP<R>) == NW * sizeof(R), "CP holds rates only");
   __shared__ CP<R> s_cp;
-  if (threadIdx.x < NW) {
+  {
     const CP<R>* src;
     if constexpr (std::is_same<R, double>::value) src = &mm->rd;
     else src = &mm->rf;
-    reinterpret_cast<R*>(&s_cp)[threadIdx.x] = __ldg(reinterpret_cast<const R*>(src) + threadIdx.x);
+    for (int w = threadIdx.x; w < NW; w += blockDim.x)
+      reinterpret_cast<R*>(&s_cp)[w] = __ldg(reinterpret_cast<const R*>(src) + w);
   }
   __syncthreads();
   const int base = (blockIdx.x - mm->block_begin) * blockDim.x * b.cpt + threadIdx.x;

@@ -15,6 +15,8 @@
 // rebuilt populations are shifted back by subtracting M(t) before the
 // reconstruction, so that the reconstruction only sees deviations.
 #pragma once
+#include "dfloat.cuh"
+#include "fx64.cuh"
 #include "lattice.cuh"
 
 namespace lbm {
@@ -40,16 +42,14 @@ struct CP {
   // that no thread spends FP64 operations on them)
   R wt[4], wt3[4], wm3[4];
   R hs, hd;
+  // the FP64 rates split into double-float pairs on the host (used by the FP64
+  // BGK-W2 and TRT collisions, which run on the FP32 pipe; see fx64.cuh)
+  DFK dk;
 };
 
 template <int Q, int K>
 inline constexpr int WCLASS = Lat<Q>::norm2(K);
 
-// one cell's share of the conserved sums (mass rho, kinetic energy rho |u|^2 / 2),
-// taken from the moments a collision computes anyway; accumulated in FP64
-struct CellSums {
-  double rho, ke;
-};
 // drho = rho - 1 for shifted storage (kept apart so that FP32 keeps its digits), rho otherwise
 template <typename R, bool SH>
 __device__ __forceinline__ void cell_sums(CellSums* cs, R drho, R ux, R uy, R uz) {
@@ -1010,6 +1010,11 @@ __device__ __forceinline__ void collide_rr(R (&f)[Q], const CP<R>& p, CellSums* 
 // the pre-collision moments
 template <int Q, int M, typename R, bool SH>
 __device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
+  if constexpr ((M == BGK_W2 || M == TRT) && std::is_same<R, double>::value && !SH) {
+    // FP64 storage: integer moments and double-float arithmetic when every
+    // population lies in its weight's binade, else the FP64 operator below
+    if (collide_fx<Q, M == TRT>(f, p.dk, cs)) return;
+  }
   if constexpr (M == BGK_W2) collide_bgk_w2<Q, R, SH>(f, p, cs);
   else if constexpr (M == BGK_NW4) collide_nw4<Q, R, SH>(f, p, cs);
   else if constexpr (M == TRT) collide_trt<Q, R, SH>(f, p, cs);

@@ -87,43 +87,6 @@ __host__ __device__ __forceinline__ float bitsf(uint32_t u) {
   return x;
 #endif
 }
-__host__ __device__ __forceinline__ void dwords(double d, uint32_t& hw, uint32_t& lw) {
-#ifdef __CUDA_ARCH__
-  hw = (uint32_t)__double2hiint(d);
-  lw = (uint32_t)__double2loint(d);
-#else
-  uint64_t u;
-  std::memcpy(&u, &d, 8);
-  hw = (uint32_t)(u >> 32);
-  lw = (uint32_t)u;
-#endif
-}
-__host__ __device__ __forceinline__ double wordsd(uint32_t hw, uint32_t lw) {
-#ifdef __CUDA_ARCH__
-  return __hiloint2double((int)hw, (int)lw);
-#else
-  const uint64_t u = ((uint64_t)hw << 32) | lw;
-  double d;
-  std::memcpy(&d, &u, 8);
-  return d;
-#endif
-}
-__host__ __device__ __forceinline__ uint32_t funnel_l3(uint32_t lw, uint32_t hw) {
-  // (hw << 3) | (lw >> 29)
-#ifdef __CUDA_ARCH__
-  return __funnelshift_l(lw, hw, 3);
-#else
-  return (hw << 3) | (lw >> 29);
-#endif
-}
-__host__ __device__ __forceinline__ float u2f_rn(uint32_t u) {
-#ifdef __CUDA_ARCH__
-  return __uint2float_rn(u);
-#else
-  return (float)u;  // round to nearest (the default mode)
-#endif
-}
-
 // ---- error-free transformations ----
 __host__ __device__ __forceinline__ DF two_sum(float a, float b) {
   const float s = fadd(a, b);
@@ -177,47 +140,56 @@ __host__ __device__ __forceinline__ DF df_recip(DF a) {
   return fast_two_sum(r0, fmul(r0, res));
 }
 
-// ---- conversions between FP64 and double-float, on the bits ----
-// Valid for |d| in [2^-74, 2^127]; smaller magnitudes (zero included) are
-// taken as +-2^-74 (an absolute error below 5.3e-23), larger ones are not
-// supported.  hi keeps the sign, exponent and leading 24 significand bits of d
-// (truncated); lo is the remaining 29 bits, rounded to nearest FP32:
-// |d - (hi + lo)| <= 2^-48 |d|.
-__host__ __device__ __forceinline__ DF df_from_double(double d) {
-  uint32_t hw, lw;
-  dwords(d, hw, lw);
-  const uint32_t sign = hw & 0x80000000u;
-  uint32_t mag = hw & 0x7fffffffu;
-  mag = mag > (uint32_t)((1023 - 74) << 20) ? mag : (uint32_t)((1023 - 74) << 20);
-  lw = mag == (uint32_t)((1023 - 74) << 20) ? 0u : lw;
-  // rebias the exponent (1023 -> 127) in place, then shift the top 23
-  // significand bits into FP32 position
-  const uint32_t hb = funnel_l3(lw, mag - (896u << 20)) | sign;
-  // lo = (remaining 29 bits) x 2^(e - 52), with the sign of d
-  const uint32_t scale = (hb & 0xff800000u) - (52u << 23);
-  const float lo = fmul(u2f_rn(lw & 0x1fffffffu), bitsf(scale));
-  return {bitsf(hb), lo};
+// ---- conversions ----
+// On B300 every conversion from or to a 64-bit type (cvt.f32.s64,
+// cvt.s64.f32, cvt.f64.*) runs at the FP64 rate (measured ~2 per SM per
+// clock), while 32-bit integer -> FP32 conversions and FP32 additions run at
+// 32 to 64 times that, so 64-bit integers are converted in 21- and 32-bit
+// pieces.
+//
+// 64-bit integer (|x| < 2^62) -> normalised double-float:
+// x = a 2^42 + b 2^21 + c with 21-bit b, c; each piece is exact in FP32, the
+// first two are summed error-free, and the result is renormalised, so
+// |x - (hi + lo)| <= 2^-47 |x| and |lo| <= ulp(hi) / 2
+__device__ __forceinline__ DF i64_to_df(long long x) {
+  const int a = (int)(x >> 42);
+  const int b = (int)((x >> 21) & 0x1fffff);
+  const int c = (int)(x & 0x1fffff);
+  const DF s = two_sum(fmul(__int2float_rn(a), 0x1p42f), fmul(__int2float_rn(b), 0x1p21f));
+  return fast_two_sum(s.hi, fadd(s.lo, __int2float_rn(c)));
 }
-
-// exact FP64 value of a normal FP32 number (integer operations only; zero and
-// subnormals give 2^-127 or so in magnitude instead, below 1e-38)
-__host__ __device__ __forceinline__ double f2d_bits(float x) {
-  const uint32_t b = fbits(x);
-  const uint32_t hw = (((b & 0x7fffffffu) >> 3) + (896u << 20)) | (b & 0x80000000u);
-  return wordsd(hw, b << 29);
+// double-float -> nearest 64-bit integer (each of two parts rounded to
+// nearest: |error| <= 1), for |hi| < 2^53 and |lo| < 2^31: the multiple of
+// 2^32 nearest to hi comes from a magic-number rounding (1.5 2^23 + v rounds v
+// to an integer and holds it in its low significand bits), the rest of hi
+// (exact, |r| <= 2^31) and lo from 32-bit conversions
+__device__ __forceinline__ long long df_round_i64(DF y) {
+  const float t = ffma(y.hi, 0x1p-32f, 12582912.0f);
+  const int n = (int)(fbits(t) - 0x4b400000u);
+  const float r = ffma(-fsub(t, 12582912.0f), 0x1p32f, y.hi);
+  return (long long)((unsigned long long)(long long)n << 32) + (long long)__float2int_rn(r) +
+         (long long)__float2int_rn(y.lo);
 }
-// nearest FP64 to hi + lo: both converted exactly, then one FP64 addition
-__host__ __device__ __forceinline__ double df_to_double(DF a) {
-#ifdef __CUDA_ARCH__
-  return __dadd_rn(f2d_bits(a.hi), f2d_bits(a.lo));
-#else
-  return f2d_bits(a.hi) + f2d_bits(a.lo);
-#endif
-}
-// split of a host-side FP64 constant (exact-ish: rounded hi, rounded remainder)
-__host__ __device__ __forceinline__ DF df_const(double d) {
+// a x 2^s for a power of two 2^s (exact while no part leaves the normal range)
+__host__ __device__ __forceinline__ DF df_scale(DF a, float p2) { return {fmul(a.hi, p2), fmul(a.lo, p2)}; }
+// host split of an FP64 constant: hi rounded to FP32, lo the rounded remainder
+// (|d - (hi + lo)| <= 2^-48 |d|)
+inline DF df_split(double d) {
   const float hi = (float)d;
   return {hi, (float)(d - (double)hi)};
 }
+
+// the FP64 relaxation rates prepared for the FP64 BGK-W2 and TRT collisions
+// that run on the FP32 pipe (fx64.cuh): double-float copies (split on the
+// host) and, per weight class c, the FP64 constant W_c = w t_c as a bit pattern
+// with the factor that takes grid units to W_c's units in the last place
+struct DFK {
+  DF omc, hs, hd, pad;
+  DF wt[4], wt3[4], wm3[4];
+  long long wbits[4];
+  float yscale[4];
+  double omc64;         // 1 - w
+  double trt_a, trt_b;  // TRT: (1 - w)/2 + (1 - w-)/2 and (1 - w)/2 - (1 - w-)/2
+};
 
 }  // namespace lbm

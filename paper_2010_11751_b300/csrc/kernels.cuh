@@ -50,6 +50,7 @@ struct KArgs {
   double omega, omc, wplus, wminus, omega_high, trt_minus;
   // per weight class c = |c|^2: w t_c, 3 w t_c, 3 w- t_c; and (1 - w)/2, (1 - w-)/2
   double wt[4], wt3[4], wm3[4], hs, hd;
+  DFK dk;  // the same rates as double-float pairs (derived_dfk)
 };
 
 // rate constants derived from w and w- (on the host: the kernels' launch
@@ -67,6 +68,27 @@ __host__ __device__ inline void derived_rates(double omega, double trt_minus, do
   }
   hs = 0.5 * (1.0 - omega);
   hd = 0.5 * (1.0 - trt_minus);
+}
+
+// the FP64 rates prepared for the FP32-pipe FP64 collisions (host)
+template <int Q>
+inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4], const double (&wm3)[4], double hs,
+                       double hd) {
+  DFK k;
+  k.omc = df_split(omc);
+  k.hs = df_split(hs);
+  k.hd = df_split(hd);
+  k.pad = {0.0f, 0.0f};
+  for (int c = 0; c < 4; ++c) {
+    k.wt[c] = df_split(wt[c]);
+    k.wt3[c] = df_split(wt3[c]);
+    k.wm3[c] = df_split(wm3[c]);
+  }
+  fx_class_constants(Q, wt, k);
+  k.omc64 = omc;
+  k.trt_a = hs + hd;
+  k.trt_b = hs - hd;
+  return k;
 }
 
 // ---------------------------------------------------------------------------
@@ -336,6 +358,7 @@ __device__ __forceinline__ CP<typename Store<P>::R> rates(const KArgs& a) {
   }
   cp.hs = R(a.hs);
   cp.hd = R(a.hd);
+  cp.dk = a.dk;
   return cp;
 }
 

@@ -90,6 +90,12 @@ __host__ __device__ constexpr int mono_at_e(int j, int k) {
          ipow_c(Lat<Q>::e(k, 2), basis_exp(Q, j, 2));
 }
 
+// one cell's share of the conserved sums (mass rho, kinetic energy rho |u|^2 / 2),
+// taken from the moments a collision computes anyway; accumulated in FP64
+struct CellSums {
+  double rho, ke;
+};
+
 // storage types: FP64 stores f; FP32 / FP16 store the shifted g = f - t_k
 enum Prec : int { F64 = 0, F32 = 1, F16 = 2 };
 
