@@ -39,9 +39,13 @@ struct BatchArgs {
 // because the member's pointers and sizes come from a table in global memory
 // and live in registers (a single-lattice kernel reads them from its launch
 // parameters)
+// (the FP64 D3Q27 BGK-W2 and TRT batch kernels, which hold 27 populations and
+// the member's addressing beside the integer and double-float state of
+// fx64.cuh, take the full register file instead of spilling; the autotuner
+// picks their block size)
 template <int Q, int M, int P>
 inline constexpr int BATCH_MIN_BLOCKS =
-    P == F64 ? 2
+    P == F64 ? ((Q == 27 && (M == BGK_W2 || M == TRT)) ? 1 : 2)
              : (MIN_BLOCKS<Q, M, P> == 1 ? 1 : (Q == 19 ? 4 : 3));
 
 // one kernel per AA step kind (SK = K_AA_EVEN or K_AA_ODD), so that each holds

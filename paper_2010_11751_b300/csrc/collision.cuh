@@ -1006,15 +1006,15 @@ __device__ __forceinline__ void collide_rr(R (&f)[Q], const CP<R>& p, CellSums* 
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
+// models and storage with the FP32-pipe FP64 operator of fx64.cuh (tried first;
+// the operators below take the cells it declines)
+template <int M, typename R, bool SH>
+inline constexpr bool HAS_FX = (M == BGK_W2 || M == TRT) && std::is_same<R, double>::value && !SH;
+
 // cs (optional): receives the cell's share of the conserved sums, computed from
 // the pre-collision moments
 template <int Q, int M, typename R, bool SH>
 __device__ __forceinline__ void collide(R (&f)[Q], const CP<R>& p, CellSums* cs = nullptr) {
-  if constexpr ((M == BGK_W2 || M == TRT) && std::is_same<R, double>::value && !SH) {
-    // FP64 storage: integer moments and double-float arithmetic when every
-    // population lies in its weight's binade, else the FP64 operator below
-    if (collide_fx<Q, M == TRT>(f, p.dk, cs)) return;
-  }
   if constexpr (M == BGK_W2) collide_bgk_w2<Q, R, SH>(f, p, cs);
   else if constexpr (M == BGK_NW4) collide_nw4<Q, R, SH>(f, p, cs);
   else if constexpr (M == TRT) collide_trt<Q, R, SH>(f, p, cs);

@@ -186,6 +186,7 @@ inline DF df_split(double d) {
 struct DFK {
   DF omc, hs, hd, pad;
   DF wt[4], wt3[4], wm3[4];
+  DF wm[4];  // w- t_c (TRT antisymmetric rate times the weight)
   long long wbits[4];
   float yscale[4];
   double omc64;         // 1 - w

@@ -21,15 +21,15 @@
 //    q = 3 w t_c (e.j), so that w E_k = w t_k + P +- q.  These are deviations
 //    of size |g| rather than |f|, so each lazy double-float operation errs by
 //    ~2^-47 |g|.
-//  * w E_k as an FP64 number without FP64 arithmetic: P and q, rounded to the
-//    units in the last place of the FP64 constant W_c = w t_c, are added as
-//    integers to W_c's bit pattern.  If the sum leaves W_c's binade (or P, q
-//    are too large for the integer rounding), w E_k is formed with FP64
-//    additions instead.
+//  * w E_k as an FP64 number without FP64 arithmetic: w t_c A, (e.v) q and q,
+//    each rounded to the units in the last place of the FP64 constant
+//    W_c = w t_c, are added as integers to W_c's bit pattern.
 //
 // A cell with any population outside its weight's binade (strong
-// non-equilibrium, high Mach number) is updated by the plain FP64 operator
-// (the caller's fallback).  Both paths compute the update of Section 2.6 to
+// non-equilibrium, high Mach number), or one whose w E_k leaves W_c's binade,
+// is updated by the plain FP64 operator instead (the caller reloads its
+// populations in the second case: every scheme's step reads and writes a
+// cell's slots from the same thread, so they are still in memory).  Both paths compute the update of Section 2.6 to
 // within a few FP64 rounding errors; which one a cell takes depends only on
 // its own populations, so every scheme (they differ only in where they load
 // and store) still produces bit-identical results.
@@ -97,28 +97,22 @@ __device__ __forceinline__ long long fx_units(DF y, bool& ok) {
   return df_round_i64(y);
 }
 
-// w E = W_c + P + S q (S = +-1) as an FP64 number, from the rounded units of
-// P and q; with FP64 additions where the integer route does not apply
-template <int Q, int S>
-__device__ __forceinline__ double fx_weq(const DFK& k_, int c, long long pi, long long qi, bool ok, const DF& P,
-                                         const DF& q) {
-  const long long b = k_.wbits[c] + pi + (S > 0 ? qi : -qi);
-  if (ok && ((unsigned long long)(b ^ k_.wbits[c]) >> 52) == 0ull) return __longlong_as_double(b);
-  const double p = __dadd_rn((double)P.hi, (double)P.lo), qq = __dadd_rn((double)q.hi, (double)q.lo);
-  const double dev = __dmul_rn(S > 0 ? __dadd_rn(p, qq) : __dsub_rn(p, qq), fx_pow2(fx_grid(Q)));
-  return __dadd_rn(__longlong_as_double(k_.wbits[c]), dev);
-}
+// outcome of collide_fx
+enum FxStatus : int {
+  FX_SKIPPED = 0,  // a population outside its weight's binade: f untouched, use the FP64 operator
+  FX_DONE = 1,     // f holds the post-collision populations
+  FX_REDO = 2      // some w E_k left W_c's binade: f is clobbered, reload it and use the FP64 operator
+};
 
-// false (and f untouched) when some population is outside its weight's binade
 template <int Q, bool TRT_>
-__device__ __forceinline__ bool collide_fx(double (&f)[Q], const DFK& k_, CellSums* cs) {
+__device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSums* cs) {
   constexpr int H = Lat<Q>::H;
   unsigned acc = 0u;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     acc |= (unsigned)__double2hiint(f[k]) ^ FxW<Q, k>::hi_tag;
   });
-  if (acc & 0xfff00000u) return false;
+  if (acc & 0xfff00000u) return FX_SKIPPED;
   // exact moments on the grid: r = rho - 1, j
   long long r, jx = 0, jy = 0, jz = 0;
   {
@@ -144,62 +138,76 @@ __device__ __forceinline__ bool collide_fx(double (&f)[Q], const DFK& k_, CellSu
   constexpr float GRID = (float)fx_pow2(fx_grid(Q));
   // rho = 1 + r, v = 1.5 j / rho (real units); A = r - v.j (grid units)
   const DF dr = i64_to_df(r);
-  const DF Jx = i64_to_df(jx), Jy = i64_to_df(jy), Jz = i64_to_df(jz);
   const DF rho = fast_two_sum(1.0f, fmul(dr.hi, GRID));
-  const DF inv15 = df_mulf(df_recip({rho.hi, fadd(rho.lo, fmul(dr.lo, GRID))}), 1.5f);
-  const DF vx = df_mul(df_scale(Jx, GRID), inv15);
-  const DF vy = df_mul(df_scale(Jy, GRID), inv15);
-  const DF vz = df_mul(df_scale(Jz, GRID), inv15);
-  const DF vj = df_add(df_add(df_mul(vx, Jx), df_mul(vy, Jy)), df_mul(vz, Jz));
-  const DF A = df_sub(dr, vj);
-  if (cs) {
-    // FP64 sums of the state read: rho = 1 + r, kinetic energy |j|^2 / (2 rho) = v.j / 3
-    cs->rho = __dadd_rn(1.0, __dmul_rn(__ll2double_rn(r), fx_pow2(fx_grid(Q))));
-    cs->ke = __dmul_rn(__dadd_rn((double)vj.hi, (double)vj.lo), fx_pow2(fx_grid(Q)) / 3.0);
-  }
-  const double omc = k_.omc64;
+  const DF rho_r = {rho.hi, fadd(rho.lo, fmul(dr.lo, GRID))};
+  const DF inv15 = df_mulf(df_recip(rho_r), 1.5f);
+  DF vx, vy, vz, A;
   {
-    const DF wtA = df_mul(k_.wt[0], A);
-    bool ok = true;
-    const long long pi = fx_units(df_scale(wtA, k_.yscale[0]), ok);
-    f[H] = fma(omc, f[H], fx_weq<Q, 1>(k_, 0, pi, 0, ok, wtA, DF{0.0f, 0.0f}));
+    const DF Jx = i64_to_df(jx), Jy = i64_to_df(jy), Jz = i64_to_df(jz);
+    vx = df_mul(df_scale(Jx, GRID), inv15);
+    vy = df_mul(df_scale(Jy, GRID), inv15);
+    vz = df_mul(df_scale(Jz, GRID), inv15);
+    const DF vj = df_add(df_add(df_mul(vx, Jx), df_mul(vy, Jy)), df_mul(vz, Jz));
+    A = df_sub(dr, vj);
+    if (cs) {
+      // FP64 sums of the state read: rho = 1 + r, kinetic energy |j|^2 / (2 rho) = v.j / 3
+      cs->rho = __dadd_rn(1.0, __dmul_rn(__ll2double_rn(r), fx_pow2(fx_grid(Q))));
+      cs->ke = __dmul_rn(__dadd_rn((double)vj.hi, (double)vj.lo), fx_pow2(fx_grid(Q)) / 3.0);
+    }
   }
+  // per weight class c (in W_c's last-place units): the bit pattern of
+  // W_c + w t_c A, and 3 w t_c (e.j) = (2 w t_c rho / GRID) (e.v) -- likewise
+  // 3 w- t_c (e.j) for TRT -- so that j is no longer needed.  The pairs come in
+  // class order (|c|^2 = 1, 2, 3), and each class's constants are formed at
+  // its first pair, so that only one class's are live at a time.
+  bool ok = true;
+  const DF rho2 = df_scale(rho_r, 2.0f / GRID);
+  auto base_of = [&](int c) { return k_.wbits[c] + fx_units(df_scale(df_mul(k_.wt[c], A), k_.yscale[c]), ok); };
+  long long base = base_of(0);
+  DF kq{0.0f, 0.0f}, kqm{0.0f, 0.0f};
+  // w E_k = W_c + w t_c A + (e.v) q +- q, assembled on W_c's bit pattern; the
+  // high words of every result are checked against W_c's sign and exponent
+  unsigned off = (unsigned)((base ^ k_.wbits[0]) >> 32);
+  const double omc = k_.omc64;
+  f[H] = fma(omc, f[H], __longlong_as_double(base));
   static_for<0, H>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
     constexpr int c = Lat<Q>::norm2(k);
-    // e.v and e.j (components of e are -1, 0 or 1)
-    DF ev{0.0f, 0.0f}, ej{0.0f, 0.0f};
+    static_assert(k == 0 || Lat<Q>::norm2(k - 1) <= c, "pairs in class order");
+    if constexpr (k == 0 || Lat<Q>::norm2(k - 1) != c) {
+      base = base_of(c);
+      kq = df_scale(df_mul(k_.wt[c], rho2), k_.yscale[c]);
+      if constexpr (TRT_) kqm = df_scale(df_mul(k_.wm[c], rho2), k_.yscale[c]);
+    }
+    // e.v (components of e are -1, 0 or 1)
+    DF ev{0.0f, 0.0f};
     bool first = true;
-    auto add_c = [&](const DF& v, const DF& j, int sign) {
-      const DF sv = sign > 0 ? v : df_neg(v), sj = sign > 0 ? j : df_neg(j);
+    auto add_c = [&](const DF& v, int sign) {
+      const DF sv = sign > 0 ? v : df_neg(v);
       ev = first ? sv : df_add(ev, sv);
-      ej = first ? sj : df_add(ej, sj);
       first = false;
     };
-    if constexpr (ex != 0) add_c(vx, Jx, ex);
-    if constexpr (ey != 0) add_c(vy, Jy, ey);
-    if constexpr (ez != 0) add_c(vz, Jz, ez);
-    const DF qp = df_mul(k_.wt3[c], ej);                       // 3 w t (e.j)
-    const DF P = df_add(df_mul(ev, qp), df_mul(k_.wt[c], A));  // w t A + (e.v) q
-    const DF q = TRT_ ? df_mul(k_.wm3[c], ej) : qp;            // antisymmetric part
-    bool ok = true;
-    const float ys = k_.yscale[c];
-    const long long pi = fx_units(df_scale(P, ys), ok);
-    const long long qi = fx_units(df_scale(q, ys), ok);
-    const double Ep = fx_weq<Q, 1>(k_, c, pi, qi, ok, P, q);   // w E along +e
-    const double Em = fx_weq<Q, -1>(k_, c, pi, qi, ok, P, q);  // w E along -e
+    if constexpr (ex != 0) add_c(vx, ex);
+    if constexpr (ey != 0) add_c(vy, ey);
+    if constexpr (ez != 0) add_c(vz, ez);
+    const DF qp = df_mul(kq, ev);                       // 3 w t (e.j), W_c units
+    const DF q = TRT_ ? df_mul(kqm, ev) : qp;           // antisymmetric part
+    const long long pi = fx_units(df_mul(ev, qp), ok);  // (e.v) 3 w t (e.j)
+    const long long qi = fx_units(q, ok);
+    const long long bp = base + pi + qi, bm = base + pi - qi;
+    off |= (unsigned)((bp ^ k_.wbits[c]) >> 32) | (unsigned)((bm ^ k_.wbits[c]) >> 32);
     const double fp = f[k + H + 1], fm = f[k];
     if constexpr (TRT_) {
       // (1-w)/2 (f+ + f-) +- (1-w-)/2 (f+ - f-), one population at a time
-      f[k + H + 1] = fma(k_.trt_a, fp, fma(k_.trt_b, fm, Ep));
-      f[k] = fma(k_.trt_a, fm, fma(k_.trt_b, fp, Em));
+      f[k + H + 1] = fma(k_.trt_a, fp, fma(k_.trt_b, fm, __longlong_as_double(bp)));
+      f[k] = fma(k_.trt_a, fm, fma(k_.trt_b, fp, __longlong_as_double(bm)));
     } else {
-      f[k + H + 1] = fma(omc, fp, Ep);
-      f[k] = fma(omc, fm, Em);
+      f[k + H + 1] = fma(omc, fp, __longlong_as_double(bp));
+      f[k] = fma(omc, fm, __longlong_as_double(bm));
     }
   });
-  return true;
+  return (ok && (off & 0xfff00000u) == 0u) ? FX_DONE : FX_REDO;
 }
 
 }  // namespace lbm

@@ -83,6 +83,7 @@ inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4]
     k.wt[c] = df_split(wt[c]);
     k.wt3[c] = df_split(wt3[c]);
     k.wm3[c] = df_split(wm3[c]);
+    k.wm[c] = df_split(wm3[c] / 3.0);
   }
   fx_class_constants(Q, wt, k);
   k.omc64 = omc;
@@ -386,20 +387,34 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
     else step_load<Q, P, L, SK, false>(a, i, f, fl);
   }
   const CP<R> cp = rate_fn();
-  collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
+  if constexpr (HAS_FX<M, R, Store<P>::shifted>) {
+    const int st = collide_fx<Q, M == TRT>(f, cp.dk, cs);
+    if (st != FX_DONE) {
+      if (st == FX_REDO) {
+        // f was overwritten: the cell's slots still hold its populations
+        if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
+        else step_load<Q, P, L, SK, false>(a, i, f, fl);
+      }
+      collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
+    }
+  } else {
+    collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
+  }
   if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
   else step_store<Q, P, L, SK, false>(a, i, f, fl);
 }
 
 // FP32/FP16 kernels of the light models are bound by memory latency: capping
 // registers so that six (D3Q19) or four (D3Q27) 256-thread blocks fit per SM
-// measured fastest.  The moment models would spill under such caps, and FP64
-// kernels are bound by the FP64 pipe: both keep the default register budget.
-// FP64 kernels are capped at two blocks per SM (<= 128 registers) so that a
-// few warps per scheduler hide the FP64 pipe latency.
+// measured fastest.  The moment models would spill under such caps: they keep
+// the default register budget.  FP64 kernels are capped at two blocks per SM
+// (<= 128 registers) so that a few warps per scheduler hide the FP64 pipe
+// latency; the D3Q19 BGK-W2 and TRT ones, whose collision runs mostly on the
+// FP32 and integer pipes (fx64.cuh) and is bound by latency, at three
+// (<= 80 registers, no spills: 10.4 -> 13.2 GLUPS for the 256^3 cavity).
 template <int Q, int M, int P>
 inline constexpr int MIN_BLOCKS =
-    P == F64 ? 2
+    P == F64 ? ((Q == 19 && (M == BGK_W2 || M == TRT)) ? 3 : 2)
              : (!(M == BGK_W2 || M == TRT || M == REG) ? 1 : (Q == 19 ? (M == TRT ? 5 : 6) : 4));
 // threads per block of the single-lattice step kernels
 inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }
@@ -425,8 +440,13 @@ __host__ __device__ constexpr int sum_cells_per_thread(int P) { return P == F64 
 // energy of the fluid cells it reads (the collision's own moments), and writes
 // them to partials[2 * block], partials[2 * block + 1] in a fixed order; a
 // block covers sum_cells_per_thread(P) x blockDim.x consecutive cells
+// the summing kernels hold four cells' sums per thread in FP64: two blocks per
+// SM (<= 128 registers) keep them out of local memory
+template <int Q, int M, int P>
+inline constexpr int SUM_MIN_BLOCKS = P == F64 ? 2 : MIN_BLOCKS<Q, M, P>;
+
 template <int Q, int M, int P, int L, int SK>
-__global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_sum_kernel(KArgs a, double* partials) {
+__global__ void __launch_bounds__(256, SUM_MIN_BLOCKS<Q, M, P>) step_sum_kernel(KArgs a, double* partials) {
   constexpr int CPT = sum_cells_per_thread(P);
   const int base = blockIdx.x * blockDim.x * CPT + threadIdx.x;
   double m = 0.0, e = 0.0;
