@@ -34,28 +34,38 @@ from paper_2010_11751_b300 import inputs as I  # noqa: E402
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
-# FP64 operations executed per fluid-cell update by the AA step kernels (ncu: dadd, dmul and dfma
-# thread instructions per launch / fluid cells, D3Q19 cavity 128^3; the even and odd kernels
-# execute the same counts).  The FP64 kernels are bound by the FP64 pipe, which issues one
-# DADD, DMUL or DFMA per slot, so the roofline counts operations (flops are reported beside).
+# FP64 pipe operations (DADD, DMUL, DFMA thread instructions) per fluid-cell update of the AA step
+# kernels, D3Q19/D3Q27 cavity 128^3, from one ncu capture per model (the even and odd kernels execute
+# the same counts).  The plain FP64 operators (RR, K, ...) are bound by the FP64 pipe, which issues
+# one of them per slot, so their roofline counts operations (flops are reported beside).  BGK-W2 and
+# TRT run their collision on the FP32 and integer pipes (exact integer moments, double-float
+# equilibrium) and keep one or two FP64 FMAs per population: they are bound by memory.
 FP64_OPS_PER_FLUID_CELL = {
     # (lattice, collision): (dadd, dmul, dfma) per fluid cell
-    (19, "BGK_W2"): (70.24, 17.00, 37.00),
-    (19, "TRT"): (70.24, 26.00, 37.00),
+    (19, "BGK_W2"): (0.24, 0.00, 19.00),
+    (19, "TRT"): (0.24, 0.00, 37.00),
+    (19, "RR"): (74.24, 40.00, 96.00),
+    (19, "K"): (81.24, 31.00, 111.00),
+    (27, "BGK_W2"): (0.43, 0.00, 27.00),
+    (27, "K"): (161.43, 67.00, 187.00),
 }
-# B300 FP64 pipe: 2 DFMA (or DADD / DMUL) per SM per clock (ncu peak_sustained: 296 thread
-# operations per cycle for 148 SMs)
-FP64_OPS_PER_CLK = 296
+# models whose FP64 collision runs off the FP64 pipe (memory-bound roofline)
+FP64_OFF_PIPE = {"BGK_W2", "TRT"}
+# B300 FP64 pipe: 2 DFMA (or DADD / DMUL) per SM per clock (ncu peak_sustained)
+FP64_OPS_PER_SM_CLK = 2
 # time budget of the reference arm (the FP64 CPU oracle timed on the host cores)
 REFERENCE_SECONDS = 120.0
-# DRAM bytes (read + write) per launch of the dominant step kernel, from one ncu capture
-# (profiles/*.md).  Reported only while the kernel sources hash to the value recorded with the
-# capture; any later kernel change turns the figure back to null.
-KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh"]
+# DRAM bytes (read + write) per launch of the dominant step kernel, from one ncu capture of the
+# D3Q19 128^3 cavity (the small case the capture rules allow), scaled to a full launch by the number
+# of cells (the kernel touches each cell's populations once: traffic grows with the cell count).
+# Reported only while the kernel sources hash to the value recorded with the capture; any later
+# kernel change turns the figure back to null.
+KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh", "fx64.cuh", "dfloat.cuh"]
 TRAFFIC = {
-    # (precision, lattice, collision, scheme, n): (bytes per AA-odd launch, source hash)
-    ("f64", 19, "BGK_W2", "aa", 256): (2544761600 + 2448588032, "b623ba38d6b6dcd3"),
+    # (precision, lattice, collision, scheme): (bytes per AA-odd launch at n = 128, source hash)
+    ("f64", 19, "BGK_W2", "aa"): (315337728 + 250320384, "5d4628922600372a"),
 }
+TRAFFIC_N = 128
 
 
 def kernel_source_hash():
@@ -85,6 +95,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default=None, help="where to keep the raw nvidia-smi samples (default: temp dir)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the forms (D3Q27, precision, batching, serving) measured after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--forms", default="",
                     help="precision | batching | serving | sweep | unrolling: the forms and studies besides "
@@ -93,7 +105,8 @@ def parse():
     ap.add_argument("--trace", type=int, default=500, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrival rate (1/s)")
     ap.add_argument("--tick", type=int, default=64, help="serving: steps per tick")
-    ap.add_argument("--slot-cells", type=int, default=1 << 26, help="serving: active-cell budget")
+    ap.add_argument("--slot-cells", type=int, default=1 << 24, help="serving: active-cell budget")
+    ap.add_argument("--tick-seconds", type=float, default=0.05, help="serving: time per group and tick")
     return ap.parse_args()
 
 
@@ -245,7 +258,8 @@ def time_native(args, rank, local, pg):
     odd = [t for s, t in enumerate(per) if (first + s) % 2 == 1]
     even = [t for s, t in enumerate(per) if (first + s) % 2 == 0]
     launches_per_step = L.lbm_kernels_per_step(g.h)
-    res = dict(N=N, total_ms=total_ms, per=per, odd=odd, even=even, bpc=bpc, mass=m, energy=e,
+    res = dict(N=N, fluid=int((flags == 0).sum()), total_ms=total_ms, per=per, odd=odd, even=even, bpc=bpc,
+               mass=m, energy=e,
                clocks=clk.summary(), launches=args.steps * launches_per_step)
     g.close()
     if not args.no_e2e:
@@ -368,8 +382,7 @@ def precision_form(args):
             nu = u0 * n / 1000.0
             flags = I.periodic_flags(n, n, n)
             walls = {}
-            rho, u = I.taylor_green_fields(n, n, n, u0)
-            rho_t, u_t = torch.from_numpy(rho).cuda(), torch.from_numpy(u.ravel()).cuda()
+            rho_t, u_t = I.taylor_green_fields_torch(n, n, n, u0)
         else:
             nu = I.cavity_nu(0.02, n, 1000.0)
             flags = I.cavity_flags(n, n, n)
@@ -474,35 +487,6 @@ def batching_form(args):
     return res
 
 
-def serving_form(args):
-    """Poisson trace (mean args.rate/s and 20 % of it) of D3Q19/D3Q27 cavity or Taylor-Green
-    solves, side U[32,192], 100-2000 steps, BGK-W2 or cumulant, FP32 or FP64 (Re 100): continuous
-    batching against a plain FIFO queue (one solve at a time) on the same trace."""
-    import torch
-
-    from paper_2010_11751_b300.serve import GpuBackend, Scheduler, summarize, trace_requests
-
-    out = []
-    for rate in (args.rate, 0.2 * args.rate):
-        trace = trace_requests(I.serving_trace(args.trace, rate), reynolds=100.0)
-        for mode, limit, budget in (("continuous_batching", None, args.slot_cells),
-                                    ("fifo_queue_one_at_a_time", 1, None)):
-            be = GpuBackend()
-            sched = Scheduler(be, tick_steps=args.tick, reserve_bytes=8 << 30, max_active=limit,
-                              max_active_cells=budget)
-            t0 = time.perf_counter()
-            res = sched.run(trace)
-            wall = time.perf_counter() - t0
-            be.close()
-            torch.cuda.empty_cache()
-            s = summarize(res, wall)
-            s.update({"mode": mode, "rate_hz": rate, "ticks": sched.ticks, "max_active": sched.max_active,
-                      "slot_cells": budget,
-                      "offered_cell_updates": sum(r.side ** 3 * r.steps for r in trace)})
-            out.append(s)
-    return out
-
-
 def size_sweep(args):
     """Performance against domain size (the paper's N-dependence study, Section 3.3.3): D3Q19
     cavity N^3 for N = 16..320, AA and two-population, BGK-W2 and RR, at the given precision."""
@@ -572,6 +556,180 @@ def unrolling_form(args):
     return rows
 
 
+def time_config(Q, n, scheme, coll, prec, steps, warmup=4, reynolds=1000.0):
+    """ms per step of one lattice-driven cavity configuration (CUDA events on its stream)."""
+    import torch
+
+    from paper_2010_11751_b300 import lbm as L
+
+    omega = 1.0 / (3.0 * I.cavity_nu(0.02, n, reynolds) + 0.5)
+    stream = torch.cuda.Stream()
+    g = L.Lattice(Q, n, n, n, scheme, coll, omega, I.cavity_flags(n, n, n), precision=L.PRECISIONS[prec],
+                  wall_velocities={I.LID: (0.02, 0.0, 0.0)}, stream=stream.cuda_stream)
+    g.init_equilibrium()
+    g.step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    bpc = g.bytes_per_cell_update
+    g.close()
+    del stream
+    torch.cuda.empty_cache()
+    return ms, bpc
+
+
+def forms(args):
+    """The forms beside the headline, measured after its timed region: the D3Q27 FP64 cavity, the
+    precision form at 512^3 (FP32/FP16 shifted storage against the FP64 mode), the batching form
+    (256 uneven cavities: per-lattice loop against one launch per step) and the serving form (a short
+    trace, continuous batching against a FIFO queue, over and below capacity)."""
+    import copy
+
+    hbm, _ = peaks()
+    out = {}
+    t0 = time.perf_counter()
+    ms, bpc = time_config(27, 256, "aa", "BGK_W2", "f64", 20)
+    n3 = 256 ** 3
+    out["d3q27_cavity256_f64_aa_bgk_w2"] = {"mlups": round(n3 / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
+                                           "hbm_frac": round(bpc * n3 / (ms * 1e-3) / 1e9 / hbm, 4)}
+    a = copy.copy(args)
+    a.n, a.form_steps = 512, 200
+    out["precision_512"] = {"steps": a.form_steps, "rows": precision_form(a)}
+    a = copy.copy(args)
+    a.form_steps = 100
+    out["batching"] = batching_form(a)
+    out["serving"] = serving_compact(args)
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def serving_compact(args, count=40):
+    """A short serving trace (count requests, the configured mix), replayed over capacity (Poisson
+    args.rate/s) and below it (60 % of the request rate the over-capacity replay sustained), each by
+    continuous batching (least remaining work first, an active-cell budget of args.slot_cells, ticks of
+    args.tick_seconds per group) and by a plain FIFO
+    queue (one solve at a time).  A sample of the FP32 requests is re-run alone in FP64 (the mode
+    the parity tests tie to the oracle) for the served results' error."""
+    import torch
+
+    from paper_2010_11751_b300.serve import GpuBackend, Scheduler, summarize, trace_requests
+
+    modes = (("continuous_batching", dict(policy="shortest", tick_seconds=args.tick_seconds,
+                                          max_active_cells=args.slot_cells)),
+             ("fifo_queue_one_at_a_time", dict(policy="fifo", max_active=1)))
+    out = {"requests": count, "rows": []}
+    rate = args.rate
+    served = None
+    for label in ("over_capacity", "below_capacity"):
+        trace = trace_requests(I.serving_trace(count, rate), reynolds=100.0)
+        for mode, kw in modes:
+            be = GpuBackend()
+            sched = Scheduler(be, tick_steps=args.tick, reserve_bytes=8 << 30, **kw)
+            t0 = time.perf_counter()
+            res = sched.run(trace)
+            wall = time.perf_counter() - t0
+            be.close()
+            torch.cuda.empty_cache()
+            summ = summarize(res, wall)
+            summ.update({"trace": label, "mode": mode, "rate_hz": round(rate, 4), "ticks": sched.ticks,
+                         "max_active": sched.max_active})
+            if summ["failed"]:
+                summ["errors"] = sorted({r.error for r in res if r.error is not None})
+            out["rows"].append(summ)
+            if mode == "continuous_batching" and label == "over_capacity":
+                served = (trace, res)
+                cap = summ["completed"] / wall
+        rate = 0.6 * cap
+    # each request of the over-capacity trace alone on the GPU: its service time without any
+    # queueing or sharing (the floor of any scheduler's latency)
+    trace, res = served
+    be = GpuBackend()
+    alone = []
+    for q in trace:
+        g = be.make_lattice(q)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        g.step(q.steps)
+        torch.cuda.synchronize()
+        alone.append(time.perf_counter() - ta)
+        g.close()
+    be.close()
+    out["alone_service_s"] = {"p50": float(np.percentile(alone, 50)), "p99": float(np.percentile(alone, 99)),
+                              "mean": float(np.mean(alone))}
+    # error of served FP32 results against the same request alone in FP64
+    f32 = sorted((q for q in trace if q.precision == "f32"), key=lambda q: q.side ** 3 * q.steps)[:4]
+    be = GpuBackend()
+    errs = []
+    for q in f32:
+        r = next(x for x in res if x.id == q.id)
+        ref = dataclasses_replace(q, precision="f64")
+        g = be.make_lattice(ref)
+        g.step(ref.steps)
+        prof = be.read_result(g)["profile"]
+        g.close()
+        errs.append({"id": q.id, "lattice": q.lattice, "workload": q.workload, "collision": q.collision,
+                     "side": q.side, "steps": q.steps,
+                     "l2_rel_profile_error_vs_f64": float(np.linalg.norm(r.profile - prof) / np.linalg.norm(prof))})
+    be.close()
+    out["f32_error_vs_f64_mode"] = errs
+    return out
+
+
+def dataclasses_replace(obj, **kw):
+    import dataclasses
+
+    return dataclasses.replace(obj, **kw)
+
+
+def sm_count():
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def roofline(args, r, dom_ms, hbm, src):
+    """Roofline of the dominant step kernel: HBM bytes per cell update, or FP64 pipe operations for
+    the FP64 operators bound by that pipe (with the HBM fraction beside)."""
+    N = r["N"]
+    achieved = r["bpc"] * N / (dom_ms * 1e-3) / 1e9
+    ops = FP64_OPS_PER_FLUID_CELL.get((args.lattice, args.collision)) if args.precision == "f64" else None
+    fluid = (args.n - 2) ** 3
+    clk = (r["clocks"].get("sm_max_mhz") or 2032.0) * 1e6
+    sms = sm_count()
+    fp64_peak = FP64_OPS_PER_SM_CLK * sms * clk / 1e9
+    if ops is not None and args.collision not in FP64_OFF_PIPE:
+        nops = sum(ops)
+        rate = nops * fluid / (dom_ms * 1e-3) / 1e9
+        flops = ops[0] + ops[1] + 2 * ops[2]
+        roof = {"bound": "alu", "achieved": round(rate, 1), "peak": round(fp64_peak, 1), "unit": "G FP64 op/s",
+                "frac": round(rate / fp64_peak, 4), "traffic": None,
+                "peak_source": f"derived: {FP64_OPS_PER_SM_CLK} FP64 operations (DADD, DMUL or DFMA) per SM per "
+                               f"clock x {sms} SMs x max SM clock",
+                "fp64_ops_per_fluid_cell": round(nops, 2), "flops_per_fluid_cell": round(flops, 2),
+                "hbm_achieved_gbs": round(achieved, 1), "hbm_frac": round(achieved / hbm, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
+        if ops is not None:
+            nops = sum(ops)
+            rate = nops * fluid / (dom_ms * 1e-3) / 1e9
+            roof["fp64_pipe"] = {"ops_per_fluid_cell": round(nops, 2), "achieved": round(rate, 1),
+                                 "peak": round(fp64_peak, 1), "unit": "G FP64 op/s",
+                                 "frac": round(rate / fp64_peak, 4)}
+    tr = TRAFFIC.get((args.precision, args.lattice, args.collision, args.scheme))
+    if tr is not None and tr[1] == kernel_source_hash():
+        roof["traffic"] = int(round(tr[0] * N / TRAFFIC_N ** 3))
+        roof["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                  f"{TRAFFIC_N}^3, scaled by the cell count")
+    roof["kernel"] = f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else "")
+    roof["bytes_per_cell_update"] = r["bpc"]
+    return roof
+
+
 def main():
     args = parse()
     if args.forms == "unrolling":
@@ -582,9 +740,9 @@ def main():
         print(json.dumps({"form": "size_sweep", "precision": args.precision, "rows": size_sweep(args)}))
         return
     if args.forms == "serving":
-        print(json.dumps({"form": "serving", "config": f"{args.trace} requests, Poisson {args.rate:g}/s and "
-                          f"{0.2 * args.rate:g}/s, side U[32,192], 100-2000 steps, D3Q19/D3Q27, cavity/TG, BGK/K, "
-                          "FP32/FP64, Re 100", "rows": serving_form(args)}))
+        print(json.dumps({"form": "serving", "config": f"{args.trace} requests, Poisson {args.rate:g}/s and below "
+                          "capacity, side U[32,192], 100-2000 steps, D3Q19/D3Q27, cavity/TG, BGK/K, FP32/FP64, Re 100",
+                          "result": serving_compact(args, count=args.trace)}))
         return
     if args.forms == "batching":
         if args.form_steps == 2000:
@@ -622,30 +780,7 @@ def main():
     value = aggregate_mlups(world, N, K, r["total_ms"])
     dominant = r["odd"] if (args.scheme == "aa" and r["odd"]) else r["per"]
     dom_ms = sum(dominant) / len(dominant)
-    achieved = r["bpc"] * N / (dom_ms * 1e-3) / 1e9
-    ops = FP64_OPS_PER_FLUID_CELL.get((args.lattice, args.collision)) if args.precision == "f64" else None
-    if ops is not None:
-        fluid = (args.n - 2) ** 3
-        clk = (r["clocks"].get("sm_max_mhz") or 2032.0) * 1e6
-        peak = FP64_OPS_PER_CLK * clk / 1e9
-        nops = sum(ops)
-        rate = nops * fluid / (dom_ms * 1e-3) / 1e9
-        flops = ops[0] + ops[1] + 2 * ops[2]
-        roof = {"bound": "alu", "achieved": round(rate, 1), "peak": round(peak, 1), "unit": "G FP64 op/s",
-                "frac": round(rate / peak, 4), "traffic": None,
-                "peak_source": "derived: 2 FP64 operations (DADD, DMUL or DFMA) per SM per clock x 148 SMs x max SM clock",
-                "fp64_ops_per_fluid_cell": round(nops, 2), "flops_per_fluid_cell": round(flops, 2),
-                "tflops": round(flops * fluid / (dom_ms * 1e-3) / 1e12, 4),
-                "hbm_achieved_gbs": round(achieved, 1), "hbm_frac": round(achieved / hbm, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
-    tr = TRAFFIC.get((args.precision, args.lattice, args.collision, args.scheme, args.n))
-    if tr is not None and tr[1] == kernel_source_hash():
-        roof["traffic"] = tr[0]
-        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/)"
-    roof["kernel"] = f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else "")
-    roof["bytes_per_cell_update"] = r["bpc"]
+    roof = roofline(args, r, dom_ms, hbm, src)
     line = {
         "metric": f"MLUPS ({workload_name(args)})",
         "value": round(value, 2),
@@ -665,6 +800,8 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "conserved": {"mass": r["mass"], "energy": r["energy"]},
+        # the same throughput counting fluid cells only (walls excluded)
+        "fluid_mlups": round(value * r["fluid"] / N, 2),
     }
     if args.scheme == "aa" and r["odd"] and r["even"]:
         line["per_launch_ms"] = {"even": round(sum(r["even"]) / len(r["even"]), 4),
@@ -676,6 +813,8 @@ def main():
         line["cpu_baseline"] = base
     if args.matrix:
         line["matrix"] = matrix(args)
+    if not args.no_forms and world == 1:
+        line["forms"] = forms(args)
     print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()

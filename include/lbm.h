@@ -257,6 +257,10 @@ LBM_API int lbm_batch_autotune(lbm_batch_t b, int* threads_per_block, int* cells
  * use_graph != 0 the n launches are captured once into a CUDA graph and
  * replayed by later calls with the same n and membership.  Asynchronous. */
 LBM_API int lbm_batch_step(lbm_batch_t b, int n, int use_graph);
+/* Launch the batch's steps on a caller's stream (NULL: the batch's own blocking stream).  A
+ * change of stream first waits for the steps already enqueued on the previous one; a member's
+ * work on its own stream, or on the legacy default stream, is waited for when the membership
+ * changes.  LBM_ERR_INVALID_ARG for a NULL batch, LBM_ERR_CUDA on a failed wait. */
 LBM_API int lbm_batch_set_stream(lbm_batch_t b, void* stream);
 LBM_API int lbm_batch_sync(lbm_batch_t b);
 LBM_API int lbm_batch_size(lbm_batch_t b, int* members, long long* cells);

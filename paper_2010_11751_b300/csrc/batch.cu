@@ -123,8 +123,9 @@ int upload_members(lbm_batch_s* b) {
     lbm_s* h = b->members[m];
     int rc = handle_prepare(h);
     if (rc) return rc;
-    // work the member enqueued on a stream of its own must be done first
-    if (h->stream && h->stream != bstream(b)) BCUDA(cudaStreamSynchronize(h->stream));
+    // work the member enqueued on its own stream (or on the legacy default stream, which a
+    // caller's non-blocking stream does not order with) must be done first
+    if (h->stream != bstream(b)) BCUDA(cudaStreamSynchronize(h->stream));
     Member& d = b->h_members[m];
     d.pop = h->d_pop[0];
     d.flags = h->d_flags;
@@ -339,7 +340,11 @@ int lbm_batch_step(lbm_batch_t b, int n, int use_graph) {
 
 int lbm_batch_set_stream(lbm_batch_t b, void* stream) {
   if (!b) return bfail(LBM_ERR_INVALID_ARG, "batch is NULL");
-  if ((cudaStream_t)stream != b->user_stream) drop_graph(b);
+  if ((cudaStream_t)stream != b->user_stream) {
+    // the steps already enqueued on the old stream finish before any on the new one starts
+    BCUDA(cudaStreamSynchronize(bstream(b)));
+    drop_graph(b);
+  }
   b->user_stream = (cudaStream_t)stream;
   return LBM_OK;
 }

@@ -408,6 +408,10 @@ class Batch:
     def step(self, n=1, use_graph=True):
         lbm_batch_step(self.b, n, use_graph)
 
+    def set_stream(self, stream):
+        """Launch on a caller's CUDA stream (a raw cudaStream_t value)."""
+        lbm_batch_set_stream(self.b, stream)
+
     def sync(self):
         lbm_batch_sync(self.b)
 

@@ -1,14 +1,24 @@
 """Serving form: continuous batching of lattice solves on one GPU.
 
 Requests (a lattice, a workload, a collision model, a storage precision, a side length
-and a step count) arrive over time.  The scheduler admits them first-in first-out as soon
-as free device memory allows, keeps every admitted lattice resident, and advances all of
+and a step count) arrive over time.  The scheduler admits them as soon as free device memory
+and the active-cell budget allow, keeps every admitted lattice resident, and advances all of
 them in ticks: active requests are grouped by (lattice, collision, precision), each group
 is one batch (one kernel launch per time step for all its members, on the group's own
-stream, so groups overlap on the device), and a tick advances every group by
-min(tick_steps, fewest remaining steps in the group).  Finished requests are harvested
-(conserved sums and the centre-line velocity profile read back), their memory freed, and
-waiting requests admitted in the freed space at the next tick.
+stream, so groups overlap on the device), and a tick advances every group by a number of
+steps that never overshoots its member with the fewest remaining steps.  Finished requests
+are harvested (conserved sums and the centre-line velocity profile read back), their memory
+freed, and waiting requests admitted in the freed space at the next tick.
+
+Two admission orders: "fifo" (arrival order; the head of the line waits for memory) and
+"shortest" (least work first -- cell updates weighted by the group's measured time per
+cell-step -- so that a small request arriving behind large ones is admitted and finishes early; a request that has waited longer than ``max_wait_s`` goes
+first, and while it does not fit nothing behind it is admitted, so large requests cannot
+starve).  With ``tick_seconds`` set, each group's steps per tick come from its measured time
+per cell-step (the backend's estimate), so that a tick of a slow group (an FP64 cumulant
+solve) and of a fast one take about the same time and a finished request is harvested
+without waiting for a long tick of another group.  Under "shortest" the group holding the
+request with the least remaining work runs on a high-priority CUDA stream for the tick.
 
 The scheduler is host logic only; the GPU work sits behind ``GpuBackend`` (the C ABI
 through ``lbm``), so the scheduling rules can be tested with a fake backend.
@@ -63,16 +73,22 @@ class _Active:
 
 
 class Scheduler:
-    """FIFO admission by free device memory, ticks of grouped batched steps, harvesting."""
+    """Admission by free device memory and a cell budget, ticks of grouped batched steps, harvesting."""
 
     def __init__(self, backend, tick_steps: int = 64, reserve_bytes: int = 0, clock=time.perf_counter,
-                 max_active: int | None = None, max_active_cells: int | None = None):
+                 max_active: int | None = None, max_active_cells: int | None = None, policy: str = "fifo",
+                 max_wait_s: float = 10.0, tick_seconds: float | None = None):
+        if policy not in ("fifo", "shortest"):
+            raise ValueError(f"unknown admission policy {policy!r}")
         self.backend = backend
         self.limit = max_active  # None: bounded by memory only; 1: a plain FIFO queue, one solve at a time
         # slot budget in lattice cells: enough active work to saturate the GPU without letting
         # every waiting request share it (which delays all completions); None: memory only
         self.cell_budget = max_active_cells
         self.tick_steps = int(tick_steps)
+        self.tick_seconds = tick_seconds
+        self.policy = policy
+        self.max_wait_s = float(max_wait_s)
         self.reserve = int(reserve_bytes)
         self.clock = clock
         self.pending: deque[Request] = deque()
@@ -88,29 +104,59 @@ class Scheduler:
     def offer(self, req: Request):
         self.pending.append(req)
 
+    def _order(self):
+        """Pending requests in admission order."""
+        if self.policy == "fifo":
+            return list(self.pending)
+        t = self.now()
+        aged = [r for r in self.pending if t - r.arrival_s > self.max_wait_s]
+        rest = sorted((r for r in self.pending if t - r.arrival_s <= self.max_wait_s),
+                      key=lambda r: (self._work(r), r.arrival_s))
+        return aged + rest
+
+    def _work(self, req):
+        """Work of a request: its cell updates, weighted by its group's measured time per
+        cell-step when the backend has one (an FP64 cumulant update costs several FP32 BGK ones)."""
+        est = getattr(self.backend, "step_seconds", None)
+        w = est(self.backend.group_key(req), 1) if est is not None else None
+        return req.side ** 3 * req.steps * (w if w else 1.0)
+
     def admit(self):
-        """Admit waiting requests in arrival order while they fit in free memory."""
+        """Admit waiting requests, in the policy's order, while they fit in free memory and in
+        the cell budget.  Under "fifo" the first request that does not fit stops admission; under
+        "shortest" it is passed over, unless it has waited longer than max_wait_s."""
         admitted = []
-        while self.pending and (self.limit is None or len(self.active) < self.limit):
-            req = self.pending[0]
+        for req in self._order():
+            if self.limit is not None and len(self.active) >= self.limit:
+                break
             need = self.backend.bytes_needed(req)
             if need + self.reserve > self.backend.total_bytes():
-                self.pending.popleft()
+                self.pending.remove(req)
                 t = self.now()
                 self.results.append(Result(req.id, req.arrival_s, t, t, 0, req.side ** 3,
                                            error="request larger than the device"))
                 continue
-            if need + self.reserve > self.backend.free_bytes():
-                break  # head of line waits for memory to free up
-            if self.cell_budget is not None and self.active:
-                if sum(a.req.side ** 3 for a in self.active) + req.side ** 3 > self.cell_budget:
-                    break  # head of line waits for a slot
-            self.pending.popleft()
+            fits = need + self.reserve <= self.backend.free_bytes()
+            if fits and self.cell_budget is not None and self.active:
+                fits = sum(a.req.side ** 3 for a in self.active) + req.side ** 3 <= self.cell_budget
+            if not fits:
+                if self.policy == "fifo" or self.now() - req.arrival_s > self.max_wait_s:
+                    break  # head of line (or an aged request) waits for memory or a slot
+                continue
+            self.pending.remove(req)
             h = self.backend.start(req)
             self.active.append(_Active(req, h, self.now()))
             admitted.append(req.id)
         self.max_active = max(self.max_active, len(self.active))
         return admitted
+
+    def _group_steps(self, key, members):
+        most = min(a.remaining for a in members)
+        if self.tick_seconds is not None:
+            est = self.backend.step_seconds(key, sum(a.req.side ** 3 for a in members))
+            if est is not None and est > 0.0:
+                return max(1, min(most, int(self.tick_seconds / est)))
+        return min(self.tick_steps, most)
 
     def tick(self):
         """Advance every active group once; harvest the finished requests."""
@@ -119,8 +165,14 @@ class Scheduler:
         groups: dict[tuple, list[_Active]] = {}
         for a in self.active:
             groups.setdefault(self.backend.group_key(a.req), []).append(a)
+        # the group holding the request with the least remaining work runs at high priority
+        # (with a backend that supports it), so that a short request keeps near its alone speed
+        prioritize = getattr(self.backend, "prioritize", None)
+        if prioritize is not None and self.policy == "shortest":
+            first = min(self.active, key=lambda a: (a.req.side ** 3 * a.remaining, a.req.arrival_s))
+            prioritize(self.backend.group_key(first.req))
         for key, members in groups.items():
-            n = min(self.tick_steps, min(a.remaining for a in members))
+            n = self._group_steps(key, members)
             self.backend.step(key, [a.handle for a in members], n)
             for a in members:
                 a.remaining -= n
@@ -183,6 +235,9 @@ class GpuBackend:
 
         self.L, self.torch = L, torch
         self.batches = {}
+        self.streams = {}
+        self._timed = {}  # group key -> (start event, end event, cell-steps) of its last step call
+        self._rate = {}   # group key -> seconds per cell-step (moving average)
         self._total = device_total_bytes
 
     def total_bytes(self):
@@ -229,15 +284,43 @@ class GpuBackend:
         key = self.group_key(req)
         if key not in self.batches:
             self.batches[key] = self.L.Batch()
+            # priority 0 (the default) and the highest (torch maps large negative values to it)
+            self.streams[key] = (self.torch.cuda.Stream(priority=0), self.torch.cuda.Stream(priority=-64))
+            self.batches[key].set_stream(self.streams[key][0].cuda_stream)
         self.batches[key].add(g)
         return g
 
+    def prioritize(self, key):
+        """Run group `key` on its high-priority stream from the next step on, the others on their
+        low-priority ones (the scheduler calls this between ticks, after a sync, so that no
+        group's work is in flight on the stream it leaves)."""
+        self._urgent = key
+
     def step(self, key, handles, n):
+        torch = self.torch
+        st = self.streams[key][1 if key == getattr(self, "_urgent", None) else 0]
+        self.batches[key].set_stream(st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
         self.batches[key].step(n, use_graph=False)
+        e1.record(st)
+        self._timed[key] = (e0, e1, n * sum(h.N for h in handles))
+
+    def step_seconds(self, key, cells):
+        """Estimated seconds per time step of a group of `cells` cells (None until measured).
+        Groups run concurrently on their own streams, so a measured time is the group's time
+        under the load of that tick."""
+        rate = self._rate.get(key)
+        return None if rate is None else rate * cells
 
     def sync(self):
         for b in self.batches.values():
             b.sync()
+        for key, (e0, e1, cell_steps) in self._timed.items():
+            sec = e0.elapsed_time(e1) * 1e-3 / max(cell_steps, 1)
+            old = self._rate.get(key)
+            self._rate[key] = sec if old is None else 0.5 * (old + sec)
+        self._timed.clear()
 
     def read_result(self, g):
         """Conserved sums and the centre-line x-velocity profile along z at x = y = n/2."""
@@ -267,3 +350,4 @@ class GpuBackend:
         for b in self.batches.values():
             b.close()
         self.batches.clear()
+        self.streams.clear()

@@ -126,3 +126,31 @@ def test_batch_rejects_mismatched_members():
             assert bt.size == (1, 64)
             bt.remove(a)
             assert bt.size == (1 - 1, 0)
+
+
+def test_batch_on_a_caller_stream_waits_for_member_set_up():
+    """A batch stepped on a caller's non-blocking stream (which does not order with the legacy
+    default stream) must still see its members' initialisation, enqueued on the legacy default
+    stream just before, and must wait for its own earlier steps when the stream is switched."""
+    import torch
+
+    n = 96
+    rho, u = I.taylor_green_fields_torch(n, n, n, 0.03)
+    ref = L.Lattice(19, n, n, n, "aa", "TRT", 1.7, I.periodic_flags(n, n, n), precision=L.F32)
+    ref.init_equilibrium(rho, u)
+    ref.step(6)
+    want = ref.get_populations()
+    ref.close()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream(priority=-64)
+    g = L.Lattice(19, n, n, n, "aa", "TRT", 1.7, I.periodic_flags(n, n, n), precision=L.F32)
+    with L.Batch() as b:
+        b.set_stream(s1.cuda_stream)
+        g.init_equilibrium(rho, u)  # legacy default stream, asynchronous
+        b.add(g)
+        b.step(3, use_graph=False)
+        b.set_stream(s2.cuda_stream)
+        b.step(3, use_graph=False)
+        b.sync()
+        b.remove(g)
+    assert np.array_equal(g.get_populations(), want)
+    g.close()

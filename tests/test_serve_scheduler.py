@@ -150,3 +150,64 @@ def test_cell_budget_slots():
     s2.t0 = 0.0
     s2.offer(req(9, 4, 8))  # larger than the budget alone: still admitted when nothing is active
     assert s2.admit() == [9]
+
+
+def test_shortest_work_admits_small_request_past_a_blocked_large_one():
+    be = FakeBackend(total=1000)
+    s = Scheduler(be, tick_steps=10, clock=Clock(), policy="shortest", max_wait_s=100.0)
+    s.t0 = 0.0
+    s.offer(req(0, 9, 50))   # 729 cells: fits
+    s.offer(req(1, 8, 50))   # 512: does not fit beside request 0
+    s.offer(req(2, 4, 10))   # 64: fits
+    # least work first: 2 (640 cell-steps), then 1 (25600) -- which does not fit once 2 is in?
+    assert s.admit() == [2, 1]  # 64 + 512 = 576 <= 1000; request 0 (36450) no longer fits
+    assert [r.id for r in s.pending] == [0]
+    f = Scheduler(FakeBackend(total=1000), tick_steps=10, clock=Clock(), policy="fifo")
+    f.t0 = 0.0
+    for r in (req(0, 9, 50), req(1, 8, 50), req(2, 4, 10)):
+        f.offer(r)
+    assert f.admit() == [0]  # FIFO: request 1 blocks the head of the line, 2 waits behind it
+
+
+def test_aged_request_goes_first_and_blocks_others_until_it_fits():
+    be = FakeBackend(total=1000)
+    clock = Clock()
+    s = Scheduler(be, tick_steps=10, clock=clock, policy="shortest", max_wait_s=0.5)
+    s.t0 = 0.0
+    s.offer(req(0, 9, 40, t=0.0))
+    assert s.admit() == [0]
+    s.offer(req(1, 8, 400, t=0.0))  # 512 cells: waits for 0
+    clock.t = 1.0                    # request 1 has now waited longer than max_wait_s
+    s.offer(req(2, 2, 4, t=0.9))     # tiny and recent: would fit, but the aged request goes first
+    assert s.admit() == []
+    while s.active:
+        s.tick()
+    assert s.admit() == [1, 2]
+
+
+def test_timed_ticks_use_the_backend_estimate():
+    class Timed(FakeBackend):
+        def step_seconds(self, key, cells):
+            return None if key[1] == "K" else 1e-4 * cells / 64.0
+
+    be = Timed(total=10 ** 6)
+    s = Scheduler(be, tick_steps=7, clock=Clock(), tick_seconds=0.002)
+    s.t0 = 0.0
+    s.offer(req(0, 4, 100))                # 64 cells: 1e-4 s per step -> 20 steps per tick
+    s.offer(req(1, 8, 100, lattice=27))    # other group, 512 cells: 8e-4 s per step -> 2 steps
+    s.offer(req(2, 4, 100, coll="K"))      # no estimate: tick_steps
+    s.admit()
+    s.tick()
+    got = {ids: n for _, ids, n in be.steps}
+    assert got == {(0,): 20, (1,): 2, (2,): 7}
+    s.offer(req(3, 4, 3))
+    s.admit()
+    be.steps.clear()
+    s.tick()
+    got = {ids: n for _, ids, n in be.steps}
+    assert got[(0, 3)] == 3  # never past the member with the fewest remaining steps
+
+
+def test_unknown_policy_is_refused():
+    with pytest.raises(ValueError):
+        Scheduler(FakeBackend(total=10), policy="lifo")
