@@ -363,6 +363,22 @@ __device__ __forceinline__ CP<typename Store<P>::R> rates(const KArgs& a) {
   return cp;
 }
 
+// the collision of one cell: the FP32-pipe FP64 operator first where the model
+// has one (fx64.cuh), the model's operator for the cells it declines;
+// reload(f) refills f with the cell's pre-collision populations (called only
+// when the first attempt had already overwritten them)
+template <int Q, int M, int P, class Reload>
+__device__ __forceinline__ void collide_cell(typename Store<P>::R (&f)[Q], const CP<typename Store<P>::R>& cp,
+                                             CellSums* cs, Reload&& reload) {
+  using R = typename Store<P>::R;
+  if constexpr (HAS_FX<M, R, Store<P>::shifted>) {
+    const int st = collide_fx<Q, M == TRT>(f, cp.dk, cs);
+    if (st == FX_DONE) return;
+    if (st == FX_REDO) reload(f);
+  }
+  collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
+}
+
 // rate_fn() yields the relaxation rates; it is called just before the
 // collision, so that a single-lattice kernel reads them from its launch
 // parameters without holding registers across the loads
@@ -387,19 +403,12 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
     else step_load<Q, P, L, SK, false>(a, i, f, fl);
   }
   const CP<R> cp = rate_fn();
-  if constexpr (HAS_FX<M, R, Store<P>::shifted>) {
-    const int st = collide_fx<Q, M == TRT>(f, cp.dk, cs);
-    if (st != FX_DONE) {
-      if (st == FX_REDO) {
-        // f was overwritten: the cell's slots still hold its populations
-        if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
-        else step_load<Q, P, L, SK, false>(a, i, f, fl);
-      }
-      collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
-    }
-  } else {
-    collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
-  }
+  // (a reload reads the cell's slots again: every scheme's step reads and
+  // writes a cell's slots from this thread only, and it has written none yet)
+  collide_cell<Q, M, P>(f, cp, cs, [&](R (&g)[Q]) {
+    if (fl == 0) step_load<Q, P, L, SK, true>(a, i, g);
+    else step_load<Q, P, L, SK, false>(a, i, g, fl);
+  });
   if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
   else step_store<Q, P, L, SK, false>(a, i, f, fl);
 }

@@ -237,12 +237,15 @@ __global__ void __launch_bounds__(32 * (1 + CW), STAGED_MIN_BLOCKS<Q, M, P>)
     for (int c = ct; c < cnt; c += 32 * CW) {
       if (sflags[c] != 0) continue;  // solid, or a listed cell
       R f[Q];
-      static_for<0, Q>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        const auto* run = reinterpret_cast<const typename Store<P>::S*>(buf + k * G::SEG_BYTES);
-        f[k] = Store<P>::to_r(run[s_off[k] + c]);
-      });
-      collide<Q, M, R, Store<P>::shifted>(f, cp);
+      auto fetch = [&](R (&g)[Q]) {
+        static_for<0, Q>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          const auto* run = reinterpret_cast<const typename Store<P>::S*>(buf + k * G::SEG_BYTES);
+          g[k] = Store<P>::to_r(run[s_off[k] + c]);
+        });
+      };
+      fetch(f);
+      collide_cell<Q, M, P>(f, cp, nullptr, fetch);  // a reload reads the stage again
       step_store<Q, P, SOA, SK, true>(a, base + c, f);
     }
     __syncwarp();
@@ -262,16 +265,31 @@ __global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed liste
   R f[Q];
   load_cell<Q, P, SOA, LD, false>(a, nb, a.a, f);
   const CP<R> cp = rates<P>(a);
-  collide<Q, M, R, Store<P>::shifted>(f, cp);
+  collide_cell<Q, M, P>(f, cp, nullptr, [&](R (&g)[Q]) { load_cell<Q, P, SOA, LD, false>(a, nb, a.a, g); });
   step_store_nb<Q, P, SOA, SK>(a, nb, f);
 }
 
-// tile shape per lattice: TILE cells, STAGES buffers, CW consumer warps
-template <int Q>
+// tile shape per lattice and storage: TILE cells, STAGES buffers, CW consumer warps
+template <int Q, int P>
 struct StagedShape {
   static constexpr int TILE = staged_tile(Q);
   static constexpr int STAGES = 2;
   static constexpr int CW = 8;
+};
+// FP64: 8-byte populations make a stage of 1024 cells 160 KB; tiles of one
+// cell per consumer thread keep two stages of two (D3Q19) or three (D3Q27)
+// blocks per SM
+template <>
+struct StagedShape<19, F64> {
+  static constexpr int TILE = 256;
+  static constexpr int STAGES = 2;
+  static constexpr int CW = 8;
+};
+template <>
+struct StagedShape<27, F64> {
+  static constexpr int TILE = 128;
+  static constexpr int STAGES = 2;
+  static constexpr int CW = 4;
 };
 
 // one AA step (SK = K_AA_EVEN or K_AA_ODD) of the whole lattice: the staged
@@ -279,7 +297,7 @@ struct StagedShape {
 template <int Q, int M, int P, int SK>
 cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, const Listed& listed,
                                const SideStream& ss, cudaStream_t s) {
-  using Sh = StagedShape<Q>;
+  using Sh = StagedShape<Q, P>;
   using G = StageLayout<Q, P, Sh::TILE, Sh::STAGES>;
   constexpr int threads = 32 * (1 + Sh::CW);
   auto kern = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW>;
@@ -316,17 +334,31 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, 
   return e;
 }
 
-// staged AA step of one model, for FP16 storage (SoA); nullptr elsewhere.
-// FP16 populations are where it pays: 2-byte loads leave the one-thread-per-cell
-// kernels short of bytes in flight.  FP32 and FP64 keep those kernels (FP32
-// already runs near the HBM roof, FP64 is bound by the FP64 pipe).
+// staged AA step of one model (SoA) for FP16 storage, and for FP64 BGK-W2 and
+// TRT; nullptr elsewhere.  FP16 populations are where it pays most: 2-byte loads
+// leave the one-thread-per-cell kernels short of bytes in flight.  The FP64
+// BGK-W2 and TRT collisions (fx64.cuh) keep ~80 registers per thread busy for
+// ~1300 instructions per cell, so the one-thread-per-cell kernels hold too few
+// loads in flight to cover HBM latency; staged, the copies are in flight
+// while the consumers compute.  FP32 keeps the one-thread-per-cell kernels
+// (they run near the HBM roof), as do the FP64 moment models (FP64-pipe bound).
 template <int M>
 StagedFn staged_fn_for_model(int Q, int P, int SK) {
-  if (P != F16) return nullptr;
-  if (Q == 19) return SK == K_AA_EVEN ? &launch_staged_step<19, M, F16, K_AA_EVEN>
-                                      : (SK == K_AA_ODD ? &launch_staged_step<19, M, F16, K_AA_ODD> : nullptr);
-  if (Q == 27) return SK == K_AA_EVEN ? &launch_staged_step<27, M, F16, K_AA_EVEN>
-                                      : (SK == K_AA_ODD ? &launch_staged_step<27, M, F16, K_AA_ODD> : nullptr);
+  constexpr bool fx = M == BGK_W2 || M == TRT;
+  auto pick = [&](auto q, auto pp) -> StagedFn {
+    constexpr int QQ = decltype(q)::value, PP = decltype(pp)::value;
+    if (SK == K_AA_EVEN) return &launch_staged_step<QQ, M, PP, K_AA_EVEN>;
+    if (SK == K_AA_ODD) return &launch_staged_step<QQ, M, PP, K_AA_ODD>;
+    return nullptr;
+  };
+  using I19 = std::integral_constant<int, 19>;
+  using I27 = std::integral_constant<int, 27>;
+  if (P == F16) return Q == 19 ? pick(I19{}, std::integral_constant<int, F16>{})
+                               : (Q == 27 ? pick(I27{}, std::integral_constant<int, F16>{}) : nullptr);
+  if constexpr (fx) {
+    if (P == F64) return Q == 19 ? pick(I19{}, std::integral_constant<int, F64>{})
+                                 : (Q == 27 ? pick(I27{}, std::integral_constant<int, F64>{}) : nullptr);
+  }
   return nullptr;
 }
 
