@@ -191,6 +191,7 @@ struct DFK {
   float yscale[4];
   double omc64;         // 1 - w
   double trt_a, trt_b;  // TRT: (1 - w)/2 + (1 - w-)/2 and (1 - w)/2 - (1 - w-)/2
+  DF trt_bdf, pad2;     // trt_b as double-float
 };
 
 }  // namespace lbm

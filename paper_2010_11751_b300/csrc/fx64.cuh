@@ -4,8 +4,9 @@
 // On B300 the FP64 pipe issues 2 operations per SM per clock (so do all
 // conversions from or to 64-bit types); the plain FP64 BGK-W2 update needs
 // ~124 FP64 operations per cell, which caps it near a fifth of the HBM
-// roofline.  Here each population costs one FP64 fused multiply-add (two for
-// TRT): the relaxation f_out = (1 - w) f + w E_k itself.
+// roofline.  Here each population costs one FP64 fused multiply-add: the
+// relaxation f_out = (1 - w) f + w E_k itself (for TRT, the part relaxing at
+// the other rate joins w E_k).
 //
 //  * Moments, exactly.  A population f_k whose sign and exponent equal those
 //    of its lattice weight t_k (f_k / t_k in [0.56, 1.12] for the D3Q19 weight
@@ -164,7 +165,7 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
   const DF rho2 = df_scale(rho_r, 2.0f / GRID);
   auto base_of = [&](int c) { return k_.wbits[c] + fx_units(df_scale(df_mul(k_.wt[c], A), k_.yscale[c]), ok); };
   long long base = base_of(0);
-  DF kq{0.0f, 0.0f}, kqm{0.0f, 0.0f};
+  DF kq{0.0f, 0.0f}, kqm{0.0f, 0.0f}, kbd{0.0f, 0.0f};
   // w E_k = W_c + w t_c A + (e.v) q +- q, assembled on W_c's bit pattern; the
   // high words of every result are checked against W_c's sign and exponent
   unsigned off = (unsigned)((base ^ k_.wbits[0]) >> 32);
@@ -178,7 +179,10 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
     if constexpr (k == 0 || Lat<Q>::norm2(k - 1) != c) {
       base = base_of(c);
       kq = df_scale(df_mul(k_.wt[c], rho2), k_.yscale[c]);
-      if constexpr (TRT_) kqm = df_scale(df_mul(k_.wm[c], rho2), k_.yscale[c]);
+      if constexpr (TRT_) {
+        kqm = df_scale(df_mul(k_.wm[c], rho2), k_.yscale[c]);
+        kbd = df_scale(k_.trt_bdf, k_.yscale[c]);
+      }
     }
     // e.v (components of e are -1, 0 or 1)
     DF ev{0.0f, 0.0f};
@@ -195,17 +199,21 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
     const DF q = TRT_ ? df_mul(kqm, ev) : qp;           // antisymmetric part
     const long long pi = fx_units(df_mul(ev, qp), ok);  // (e.v) 3 w t (e.j)
     const long long qi = fx_units(q, ok);
-    const long long bp = base + pi + qi, bm = base + pi - qi;
-    off |= (unsigned)((bp ^ k_.wbits[c]) >> 32) | (unsigned)((bm ^ k_.wbits[c]) >> 32);
+    long long bp = base + pi + qi, bm = base + pi - qi;
     const double fp = f[k + H + 1], fm = f[k];
     if constexpr (TRT_) {
-      // (1-w)/2 (f+ + f-) +- (1-w-)/2 (f+ - f-), one population at a time
-      f[k + H + 1] = fma(k_.trt_a, fp, fma(k_.trt_b, fm, __longlong_as_double(bp)));
-      f[k] = fma(k_.trt_a, fm, fma(k_.trt_b, fp, __longlong_as_double(bm)));
-    } else {
-      f[k + H + 1] = fma(omc, fp, __longlong_as_double(bp));
-      f[k] = fma(omc, fm, __longlong_as_double(bm));
+      // (1-w)/2 (f+ + f-) +- (1-w-)/2 (f+ - f-) = (1 - w) f+- -+ b d, with
+      // b = (1-w)/2 - (1-w-)/2 and d = f+ - f- = g+ - g-: the difference of the
+      // two bit patterns (both in t_k's binade), exact on the grid
+      constexpr int sh = FxW<Q, k>::sh;
+      const long long d = (long long)((unsigned long long)(__double_as_longlong(fp) - __double_as_longlong(fm)) << sh);
+      const long long bd = fx_units(df_mul(kbd, i64_to_df(d)), ok);
+      bp -= bd;
+      bm += bd;
     }
+    off |= (unsigned)((bp ^ k_.wbits[c]) >> 32) | (unsigned)((bm ^ k_.wbits[c]) >> 32);
+    f[k + H + 1] = fma(omc, fp, __longlong_as_double(bp));
+    f[k] = fma(omc, fm, __longlong_as_double(bm));
   });
   return (ok && (off & 0xfff00000u) == 0u) ? FX_DONE : FX_REDO;
 }

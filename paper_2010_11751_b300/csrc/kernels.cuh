@@ -89,6 +89,8 @@ inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4]
   k.omc64 = omc;
   k.trt_a = hs + hd;
   k.trt_b = hs - hd;
+  k.trt_bdf = df_split(hs - hd);
+  k.pad2 = {0.0f, 0.0f};
   return k;
 }
 
@@ -418,12 +420,12 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
 // measured fastest.  The moment models would spill under such caps: they keep
 // the default register budget.  FP64 kernels are capped at two blocks per SM
 // (<= 128 registers) so that a few warps per scheduler hide the FP64 pipe
-// latency; the D3Q19 BGK-W2 and TRT ones, whose collision runs mostly on the
-// FP32 and integer pipes (fx64.cuh) and is bound by latency, at three
-// (<= 80 registers, no spills: 10.4 -> 13.2 GLUPS for the 256^3 cavity).
+// latency; the D3Q19 BGK-W2 ones, whose collision runs mostly on the FP32 and
+// integer pipes (fx64.cuh) and is bound by latency, at three (<= 80 registers,
+// no spills: 10.4 -> 13.2 GLUPS for the 256^3 cavity; TRT would spill there).
 template <int Q, int M, int P>
 inline constexpr int MIN_BLOCKS =
-    P == F64 ? ((Q == 19 && (M == BGK_W2 || M == TRT)) ? 3 : 2)
+    P == F64 ? ((Q == 19 && M == BGK_W2) ? 3 : 2)
              : (!(M == BGK_W2 || M == TRT || M == REG) ? 1 : (Q == 19 ? (M == TRT ? 5 : 6) : 4));
 // threads per block of the single-lattice step kernels
 inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }

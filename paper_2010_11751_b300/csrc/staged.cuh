@@ -169,12 +169,31 @@ __device__ __forceinline__ void stage_issue_lane(const KArgs& a, unsigned char* 
   }
 }
 
+// blocks per SM the register budget is sized for: two for the light models
+// (FP64: four for D3Q19 and three for D3Q27, as many as their stages fit in
+// shared memory), one for the moment models.  The budget decides whether the
+// listed-cell kernel, running beside on a second stream, finds room on the
+// SMs: at 112 registers per thread (two 9-warp D3Q19 FP64 blocks) it found
+// none and the FP64 step ran 22 % slower than at 96.
 template <int Q, int M, int P>
-inline constexpr int STAGED_MIN_BLOCKS = (M == BGK_W2 || M == TRT || M == REG) ? 2 : 1;
+inline constexpr int STAGED_BLOCKS =
+    P == F64 ? (Q == 19 ? 4 : 3) : ((M == BGK_W2 || M == TRT || M == REG) ? 2 : 1);
+// registers per thread for that many blocks of CW + 1 warps (a multiple of 8,
+// at most 255), given as an explicit cap; the FP16 light-model kernels are held
+// to 96 (two 9-warp blocks would allow 112), which leaves the listed-cell
+// kernel room beside them (512^3 cavity, D3Q19 BGK-W2: 57.1 -> 60.2 GLUPS,
+// TRT 53.2 -> 59.0)
+template <int Q, int M, int P, int CW>
+inline constexpr int STAGED_REGS =
+    (P == F16 && (M == BGK_W2 || M == TRT || M == REG))
+        ? 96
+        : ((65536 / (STAGED_BLOCKS<Q, M, P> * 32 * (1 + CW))) / 8 * 8 > 255
+               ? 255
+               : (65536 / (STAGED_BLOCKS<Q, M, P> * 32 * (1 + CW))) / 8 * 8);
 
 // one producer warp and CW consumer warps per block
 template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW>
-__global__ void __launch_bounds__(32 * (1 + CW), STAGED_MIN_BLOCKS<Q, M, P>)
+__global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
     staged_aa_kernel(KArgs a, int ntiles, int* err, long long wait_cycles) {
   using G = StageLayout<Q, P, TILE, STAGES>;
   using R = typename Store<P>::R;
@@ -276,14 +295,16 @@ struct StagedShape {
   static constexpr int STAGES = 2;
   static constexpr int CW = 8;
 };
-// FP64: 8-byte populations make a stage of 1024 cells 160 KB; tiles of one
-// cell per consumer thread keep two stages of two (D3Q19) or three (D3Q27)
-// blocks per SM
+// FP64: 8-byte populations make a stage of 1024 cells 160 KB.  128-cell tiles
+// (one cell per consumer thread), two stages and four 5-warp blocks per SM
+// measured fastest for D3Q19 (256^3 cavity: 17.6 GLUPS, against 17.4 for
+// 256-cell tiles, 16.1 for three stages and 15.2 for 64-cell tiles); D3Q27
+// runs three such blocks.
 template <>
 struct StagedShape<19, F64> {
-  static constexpr int TILE = 256;
+  static constexpr int TILE = 128;
   static constexpr int STAGES = 2;
-  static constexpr int CW = 8;
+  static constexpr int CW = 4;
 };
 template <>
 struct StagedShape<27, F64> {

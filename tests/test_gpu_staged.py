@@ -1,18 +1,19 @@
-"""Staged FP16 AA steps (bulk cells from shared-memory tiles filled by bulk asynchronous copies,
-the other fluid cells by a listed-cell kernel) against the one-thread-per-cell kernels.
+"""Staged AA steps -- FP16 for every model, FP64 for BGK-W2 and TRT -- (bulk cells from
+shared-memory tiles filled by bulk asynchronous copies, the other fluid cells by a listed-cell
+kernel) against the one-thread-per-cell kernels.
 
 Both update every cell with the same loads, collision and stores, so the AA pattern through
 the staged kernels must be bit-identical to the two-population scheme (which never stages) in
 the same storage precision, for every collision model, on lattices that span many tiles with a
 ragged last tile, walls of three kinds next to bulk cells, periodic faces, and degenerate
 sizes down to a single cell.  The FP16 result is also held to its budget against the FP64
-oracle, and the staged kernels' error word must stay clear (lbm_reduce would report
-LBM_ERR_TIMEOUT otherwise).
+oracle, the FP64 one to 1e-12, and the staged kernels' error word must stay clear (lbm_reduce
+would report LBM_ERR_TIMEOUT otherwise).
 """
 import numpy as np
 import pytest
 
-from gpu_helpers import MODELS, case, gpu_lattice, gpu_run, oracle_run, prm
+from gpu_helpers import MODELS, RTOL_F64, case, gpu_lattice, gpu_run, oracle_run, prm, rel_err
 from paper_2010_11751_b300 import inputs as I
 from paper_2010_11751_b300 import lbm as L
 
@@ -49,17 +50,39 @@ def test_staged_aa_bit_identical_to_twopop(Q, model):
         assert np.array_equal(got, base), steps
 
 
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("model", ["BGK_W2", "TRT"])
+def test_staged_fp64_bit_identical_to_twopop_and_oracle(Q, model):
+    """FP64 staged tiles (256 cells for D3Q19, 128 for D3Q27) over many tiles with a ragged last
+    one; the two-population scheme never stages."""
+    p = prm()
+    flags, f0 = case(Q, DIMS, seed=173, model=model)
+    for steps in (5, 6):
+        base = gpu_run(Q, DIMS, flags, model, p, f0, steps)
+        with gpu_lattice(Q, DIMS, flags, model, p, "aa") as g:
+            assert L.lbm_kernels_per_step(g.h) == 2  # staged kernel + listed-cell kernel
+            g.set_populations(f0)
+            g.step(steps)
+            got = g.get_populations().copy()
+            m, e = g.reduce()
+        assert np.isfinite(m) and np.isfinite(e)
+        assert np.array_equal(got, base), steps
+    ref = oracle_run(Q, DIMS, flags, model, p, f0, 6)
+    assert rel_err(got, ref.f, flags) <= RTOL_F64
+
+
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 17), (2, 3, 5), (3, 1, 40), (16, 16, 16), (1, 64, 64),
                                   (5, 7, 333)])
 @pytest.mark.parametrize("Q", [19, 27])
-def test_staged_degenerate_and_ragged_sizes(dims, Q):
+@pytest.mark.parametrize("precision", [L.F16, L.F64])
+def test_staged_degenerate_and_ragged_sizes(dims, Q, precision):
     p = prm()
     nx, ny, nz = dims
     solid = 0.15 if nx * ny * nz > 8 else 0.0
     flags, f0 = case(Q, dims, seed=181, solid=solid, model="TRT")
     for steps in (3, 4):
-        base = gpu_run(Q, dims, flags, "TRT", p, f0, steps, precision=L.F16)
-        got = gpu_run(Q, dims, flags, "TRT", p, f0, steps, scheme="aa", precision=L.F16)
+        base = gpu_run(Q, dims, flags, "TRT", p, f0, steps, precision=precision)
+        got = gpu_run(Q, dims, flags, "TRT", p, f0, steps, scheme="aa", precision=precision)
         assert np.array_equal(got, base), (dims, steps)
 
 
@@ -123,7 +146,7 @@ def test_staged_handle_reuse_and_accounting():
 
 def test_kernels_per_step_reports_the_launches():
     flags = I.cavity_flags(12, 10, 9)
-    cases = [("aa", L.F16, flags, 2), ("aa", L.F32, flags, 1), ("aa", L.F64, flags, 1), ("swap", L.F16, flags, 2),
+    cases = [("aa", L.F16, flags, 2), ("aa", L.F32, flags, 1), ("aa", L.F64, flags, 2), ("swap", L.F16, flags, 2),
              ("twopop", L.F16, flags, 1), ("esotwist", L.F16, flags, 1),
              ("aa", L.F16, np.ones(12 * 10 * 9, np.uint8), 1)]  # all solid: no listed cells
     for scheme, prec, fl, want in cases:
