@@ -459,6 +459,43 @@ int sum_blocks(const lbm_s* h) {
   return (int)((h->N + chunk - 1) / chunk);
 }
 
+// step kind of the handle's next step
+int next_step_kind(const lbm_s* h) {
+  switch (h->scheme) {
+    case LBM_TWOPOP: return K_TWOPOP;
+    case LBM_AA: return (h->steps & 1) ? K_AA_ODD : K_AA_EVEN;
+    case LBM_SWAP: return K_AA_EVEN;
+    default: return K_ESOTWIST;
+  }
+}
+
+Listed listed_of(const lbm_s* h) {
+  Listed listed;
+  listed.cell = h->d_list;
+  listed.mask = h->d_list_mask;
+  listed.kinds = h->d_list_kinds;
+  listed.n = h->nlist;
+  return listed;
+}
+
+// pairs of partial sums a summing step of the handle writes: its summing step
+// kernel's blocks, or the staged step's (0 if neither exists)
+int step_sum_parts(lbm_s* h, int* nparts) {
+  *nparts = 0;
+  const bool staged = h->scheme == LBM_AA && h->sfns[(int)(h->steps & 1)];
+  if (staged) {
+    int rc = ensure_nonbulk_list(h);
+    if (rc) return rc;
+    const cudaError_t e = h->sfns[(int)(h->steps & 1)](make_args(h), h->d_err, h->wait_cycles, listed_of(h),
+                                                       h->side, h->stream, nullptr, nparts);
+    if (e == cudaErrorNotSupported) *nparts = 0;
+    else if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+    return LBM_OK;
+  }
+  if (h->sumfns[next_step_kind(h)]) *nparts = sum_blocks(h);
+  return LBM_OK;
+}
+
 // enqueue one time step; with sum_partials, the step's kernel also writes the
 // per-block FP64 sums of the state it reads (returns the number of blocks in
 // *nparts), and the caller guarantees that a summing kernel exists
@@ -479,15 +516,11 @@ int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr
       break;
     case LBM_AA: {
       const int odd = (int)(h->steps & 1);
-      if (h->sfns[odd] && !sum_partials) {
+      if (h->sfns[odd]) {
         const int rc = ensure_nonbulk_list(h);
         if (rc) return rc;
-        Listed listed;
-        listed.cell = h->d_list;
-        listed.mask = h->d_list_mask;
-        listed.kinds = h->d_list_kinds;
-        listed.n = h->nlist;
-        e = h->sfns[odd](a, h->d_err, h->wait_cycles, listed, h->side, h->stream);
+        e = h->sfns[odd](a, h->d_err, h->wait_cycles, listed_of(h), h->side, h->stream, sum_partials,
+                         sum_partials ? nparts : nullptr);
       } else {
         e = kernel(odd ? K_AA_ODD : K_AA_EVEN);
       }
@@ -506,15 +539,6 @@ int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr
   return LBM_OK;
 }
 
-// step kind of the handle's next step
-int next_step_kind(const lbm_s* h) {
-  switch (h->scheme) {
-    case LBM_TWOPOP: return K_TWOPOP;
-    case LBM_AA: return (h->steps & 1) ? K_AA_ODD : K_AA_EVEN;
-    case LBM_SWAP: return K_AA_EVEN;
-    default: return K_ESOTWIST;
-  }
-}
 }  // namespace
 
 int lbm_step(lbm_t h, int n) {
@@ -544,9 +568,10 @@ int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
   int rc = upload_wall(h);
   if (rc) return rc;
   double* out2 = h->d_partials + 2 * h->partials;
-  const int sk = next_step_kind(h);
-  const bool staged = h->scheme == LBM_AA && h->sfns[(int)(h->steps & 1)];
-  if (staged || !h->sumfns[sk]) {
+  int parts = 0;
+  rc = step_sum_parts(h, &parts);
+  if (rc) return rc;
+  if (parts == 0) {
     // no summing kernel for this configuration: the reduction kernel reads the
     // state first, then the steps run
     KArgs a = make_args(h);
@@ -554,7 +579,7 @@ int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
     rc = lbm_step(h, n);
     if (rc) return rc;
   } else {
-    const size_t need = 2 * (size_t)sum_blocks(h);
+    const size_t need = 2 * (size_t)parts;
     if (h->sum_partials_cap < need) {
       if (h->d_sum_partials) {
         LBM_CUDA(cudaStreamSynchronize(h->stream));

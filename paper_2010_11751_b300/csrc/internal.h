@@ -38,9 +38,13 @@ struct SideStream {
 };
 // staged AA step: bulk cells through the shared-memory tile pipeline, listed
 // cells from their records; err receives the kernel's error word
-// and wait_cycles bounds each wait of its copy pipeline (SM clock cycles)
+// and wait_cycles bounds each wait of its copy pipeline (SM clock cycles).
+// With nparts set, the step also writes *nparts pairs of FP64 partial sums
+// (mass, kinetic energy) of the state it reads to partials, or, with partials
+// NULL, only returns that count (nothing is launched); a configuration without
+// summing kernels returns cudaErrorNotSupported for it.
 using StagedFn = cudaError_t (*)(const KArgs&, int* err, long long wait_cycles, const Listed& listed,
-                                 const SideStream& ss, cudaStream_t);
+                                 const SideStream& ss, cudaStream_t, double* partials, int* nparts);
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);

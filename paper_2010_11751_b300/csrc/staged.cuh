@@ -191,10 +191,15 @@ inline constexpr int STAGED_REGS =
                ? 255
                : (65536 / (STAGED_BLOCKS<Q, M, P> * 32 * (1 + CW))) / 8 * 8);
 
-// one producer warp and CW consumer warps per block
-template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW>
+// one producer warp and CW consumer warps per block.  SUMS: every consumer warp
+// also sums, in FP64, the mass and kinetic energy of the bulk cells it updates
+// (from the moments its collisions compute) and writes them to
+// partials[2 w], partials[2 w + 1] with w = blockIdx.x * CW + its index -- a
+// fixed assignment of cells to warps (the grid and its tile order are fixed),
+// so the sums are reproducible
+template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW, bool SUMS>
 __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
-    staged_aa_kernel(KArgs a, int ntiles, int* err, long long wait_cycles) {
+    staged_aa_kernel(KArgs a, int ntiles, int* err, long long wait_cycles, double* partials) {
   using G = StageLayout<Q, P, TILE, STAGES>;
   using R = typename Store<P>::R;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -238,6 +243,7 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
   // consumers: the bulk cells of each tile, from the staged runs
   const CP<R> cp = rates<P>(a);
   const int ct = threadIdx.x - 32;
+  double msum = 0.0, esum = 0.0;
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int st = it % STAGES;
@@ -264,28 +270,69 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
         });
       };
       fetch(f);
-      collide_cell<Q, M, P>(f, cp, nullptr, fetch);  // a reload reads the stage again
+      if constexpr (SUMS) {
+        CellSums cs{0.0, 0.0};
+        collide_cell<Q, M, P>(f, cp, &cs, fetch);  // a reload reads the stage again
+        msum += cs.rho;
+        esum += cs.ke;
+      } else {
+        collide_cell<Q, M, P>(f, cp, nullptr, fetch);
+      }
       step_store<Q, P, SOA, SK, true>(a, base + c, f);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_addr(smem + 8 * (STAGES + st)));  // release stage st
   }
+  if constexpr (SUMS) {
+    for (int o = 16; o > 0; o >>= 1) {
+      msum += __shfl_down_sync(0xffffffffu, msum, o);
+      esum += __shfl_down_sync(0xffffffffu, esum, o);
+    }
+    if (lane == 0) {
+      const int w = blockIdx.x * CW + (warp - 1);
+      partials[2 * w] = msum;
+      partials[2 * w + 1] = esum;
+    }
+  }
 }
 
-// the listed cells, one thread each, from their records
-template <int Q, int M, int P, int SK>
-__global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed listed) {
+// the listed cells, one thread each, from their records.  SUMS: each 128-thread
+// block writes the FP64 mass and kinetic energy of its cells to
+// partials[2 b], partials[2 b + 1] (warp trees, then the four warps in order)
+template <int Q, int M, int P, int SK, bool SUMS>
+__global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed listed, double* partials) {
   using R = typename Store<P>::R;
   constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : LD_LOCAL;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= listed.n) return;
-  const NbRec nb(__ldg(listed.cell + t), a, __ldg(listed.mask + t), __ldg(listed.kinds + 2 * (size_t)t),
-                 __ldg(listed.kinds + 2 * (size_t)t + 1));
-  R f[Q];
-  load_cell<Q, P, SOA, LD, false>(a, nb, a.a, f);
-  const CP<R> cp = rates<P>(a);
-  collide_cell<Q, M, P>(f, cp, nullptr, [&](R (&g)[Q]) { load_cell<Q, P, SOA, LD, false>(a, nb, a.a, g); });
-  step_store_nb<Q, P, SOA, SK>(a, nb, f);
+  CellSums cs{0.0, 0.0};
+  if (t < listed.n) {
+    const NbRec nb(__ldg(listed.cell + t), a, __ldg(listed.mask + t), __ldg(listed.kinds + 2 * (size_t)t),
+                   __ldg(listed.kinds + 2 * (size_t)t + 1));
+    R f[Q];
+    load_cell<Q, P, SOA, LD, false>(a, nb, a.a, f);
+    const CP<R> cp = rates<P>(a);
+    collide_cell<Q, M, P>(f, cp, SUMS ? &cs : nullptr,
+                          [&](R (&g)[Q]) { load_cell<Q, P, SOA, LD, false>(a, nb, a.a, g); });
+    step_store_nb<Q, P, SOA, SK>(a, nb, f);
+  }
+  if constexpr (SUMS) {
+    double m = cs.rho, e = cs.ke;
+    for (int o = 16; o > 0; o >>= 1) {
+      m += __shfl_down_sync(0xffffffffu, m, o);
+      e += __shfl_down_sync(0xffffffffu, e, o);
+    }
+    __shared__ double sm[4][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+      sm[w][0] = m;
+      sm[w][1] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      partials[2 * blockIdx.x] = ((sm[0][0] + sm[1][0]) + sm[2][0]) + sm[3][0];
+      partials[2 * blockIdx.x + 1] = ((sm[0][1] + sm[1][1]) + sm[2][1]) + sm[3][1];
+    }
+  }
 }
 
 // tile shape per lattice and storage: TILE cells, STAGES buffers, CW consumer warps
@@ -314,17 +361,25 @@ struct StagedShape<27, F64> {
 };
 
 // one AA step (SK = K_AA_EVEN or K_AA_ODD) of the whole lattice: the staged
-// kernel over the bulk cells, then the listed-cell kernel
+// kernel over the bulk cells, then the listed-cell kernel; with nparts, the
+// summing variants (FP64 only), whose partial sums follow each other in
+// partials: the staged kernel's warps, then the listed kernel's blocks
 template <int Q, int M, int P, int SK>
 cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, const Listed& listed,
-                               const SideStream& ss, cudaStream_t s) {
+                               const SideStream& ss, cudaStream_t s, double* partials, int* nparts) {
   using Sh = StagedShape<Q, P>;
   using G = StageLayout<Q, P, Sh::TILE, Sh::STAGES>;
   constexpr int threads = 32 * (1 + Sh::CW);
-  auto kern = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW>;
+  constexpr bool can_sum = P == F64;
+  if (nparts && !can_sum) return cudaErrorNotSupported;
+  auto kern = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, false>;
+  auto kern_sum = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, can_sum>;
   // blocks of the persistent grid: resident blocks per SM x SMs (set once)
   static const int grid = [&] {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) != cudaSuccess) return 0;
+    if (can_sum &&
+        cudaFuncSetAttribute(kern_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) != cudaSuccess)
+      return 0;
     int occ = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, G::BYTES) != cudaSuccess) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -333,6 +388,12 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, 
   }();
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   const int ntiles = (a.N + Sh::TILE - 1) / Sh::TILE;
+  const int blocks = ntiles < grid ? ntiles : grid;
+  const int lblocks = (listed.n + 127) / 128;
+  if (nparts) {
+    *nparts = blocks * Sh::CW + (listed.n > 0 ? lblocks : 0);
+    if (!partials) return cudaSuccess;
+  }
   // the two kernels update disjoint cells: with a side stream, the listed-cell
   // kernel runs beside the staged kernel (fork after the previous step, join
   // before the next)
@@ -343,10 +404,15 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.side, ss.fork, 0);
     if (e != cudaSuccess) return e;
   }
-  if (ntiles > 0) kern<<<ntiles < grid ? ntiles : grid, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles);
+  if (ntiles > 0) {
+    if (nparts) kern_sum<<<blocks, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles, partials);
+    else kern<<<blocks, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles, nullptr);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess || listed.n <= 0) return e;
-  listed_cells_kernel<Q, M, P, SK><<<(listed.n + 127) / 128, 128, 0, side ? ss.side : s>>>(a, listed);
+  cudaStream_t ls = side ? ss.side : s;
+  if (nparts) listed_cells_kernel<Q, M, P, SK, can_sum><<<lblocks, 128, 0, ls>>>(a, listed, partials + 2 * blocks * Sh::CW);
+  else listed_cells_kernel<Q, M, P, SK, false><<<lblocks, 128, 0, ls>>>(a, listed, nullptr);
   e = cudaGetLastError();
   if (e == cudaSuccess && side) {
     e = cudaEventRecord(ss.join, ss.side);
