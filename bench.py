@@ -55,17 +55,36 @@ FP64_OFF_PIPE = {"BGK_W2", "TRT"}
 FP64_OPS_PER_SM_CLK = 2
 # time budget of the reference arm (the FP64 CPU oracle timed on the host cores)
 REFERENCE_SECONDS = 120.0
-# DRAM bytes (read + write) per launch of the dominant step kernel, from one ncu capture of the
-# D3Q19 128^3 cavity (the small case the capture rules allow), scaled to a full launch by the number
-# of cells (the kernel touches each cell's populations once: traffic grows with the cell count).
-# Reported only while the kernel sources hash to the value recorded with the capture; any later
-# kernel change turns the figure back to null.
-KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh", "fx64.cuh", "dfloat.cuh"]
+# DRAM bytes (read + write) of the AA-odd step of the headline configuration, from one ncu capture
+# of the D3Q19 128^3 cavity (the small case the capture rules allow) per cell each kernel updates:
+# the staged kernel's bulk cells and the listed-cell kernel's cells (next to a wall or on a domain
+# face); a full step's traffic is scaled from those by the cell counts of the lattice.  Reported
+# only while the kernel sources hash to the value recorded with the capture; any later kernel
+# change turns the figure back to null.
+KERNEL_SOURCES = ["lattice.cuh", "collision.cuh", "kernels.cuh", "fx64.cuh", "dfloat.cuh", "staged.cuh"]
 TRAFFIC = {
-    # (precision, lattice, collision, scheme): (bytes per AA-odd launch at n = 128, source hash)
-    ("f64", 19, "BGK_W2", "aa"): (315337728 + 250320384, "5d4628922600372a"),
+    # (precision, lattice, collision, scheme): (bytes per bulk cell, bytes per listed cell, source hash)
+    ("f64", 19, "BGK_W2", "aa"): ((319944960 + 241556992) / 124 ** 3, (67347200 + 7127808) / (126 ** 3 - 124 ** 3),
+                                  "d591fc1941bc30dd"),
 }
-TRAFFIC_N = 128
+
+
+def bulk_and_listed(flags, n, Q):
+    """Fluid cells with every lattice neighbour fluid and off the domain faces (the staged kernel's
+    bulk cells), and the other fluid cells (the listed-cell kernel's)."""
+    fl = flags.reshape(n, n, n) != 0
+    fluid = ~fl
+    near = np.zeros_like(fl)
+    for c in np.ndindex(3, 3, 3):
+        c = np.array(c) - 1
+        n2 = int((c * c).sum())
+        if n2 == 0 or (Q == 19 and n2 == 3):
+            continue
+        near |= np.roll(fl, shift=tuple(-c), axis=(0, 1, 2))
+    face = np.zeros_like(fl)
+    face[0], face[-1], face[:, 0], face[:, -1], face[:, :, 0], face[:, :, -1] = (True,) * 6
+    bulk = fluid & ~near & ~face
+    return int(bulk.sum()), int((fluid & ~bulk).sum())
 
 
 def kernel_source_hash():
@@ -260,7 +279,7 @@ def time_native(args, rank, local, pg):
     launches_per_step = L.lbm_kernels_per_step(g.h)
     res = dict(N=N, fluid=int((flags == 0).sum()), total_ms=total_ms, per=per, odd=odd, even=even, bpc=bpc,
                mass=m, energy=e,
-               clocks=clk.summary(), launches=args.steps * launches_per_step)
+               clocks=clk.summary(), launches=args.steps * launches_per_step, kernels_per_step=launches_per_step)
     g.close()
     if not args.no_e2e:
         res["e2e"] = e2e_native(args, L, torch)
@@ -721,11 +740,17 @@ def roofline(args, r, dom_ms, hbm, src):
                                  "peak": round(fp64_peak, 1), "unit": "G FP64 op/s",
                                  "frac": round(rate / fp64_peak, 4)}
     tr = TRAFFIC.get((args.precision, args.lattice, args.collision, args.scheme))
-    if tr is not None and tr[1] == kernel_source_hash():
-        roof["traffic"] = int(round(tr[0] * N / TRAFFIC_N ** 3))
-        roof["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
-                                  f"{TRAFFIC_N}^3, scaled by the cell count")
+    if tr is not None and tr[2] == kernel_source_hash():
+        _, _, flags, _ = workload(args)
+        bulk, listed = bulk_and_listed(flags, args.n, args.lattice)
+        roof["traffic"] = int(round(tr[0] * bulk + tr[1] * listed))
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the AA-odd staged and "
+                                  "listed-cell launches at 128^3, per cell each updates, scaled by this lattice's "
+                                  f"{bulk} bulk and {listed} listed cells")
     roof["kernel"] = f"{args.scheme} step" + (" (odd: neighbour pull/push)" if args.scheme == "aa" else "")
+    if r.get("kernels_per_step", 1) == 2:
+        roof["kernel"] += ("; staged bulk-cell kernel with the listed-cell kernel beside it on a second stream, "
+                           "timed together per step")
     roof["bytes_per_cell_update"] = r["bpc"]
     return roof
 

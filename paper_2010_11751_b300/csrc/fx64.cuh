@@ -30,10 +30,11 @@
 // non-equilibrium, high Mach number), or one whose w E_k leaves W_c's binade,
 // is updated by the plain FP64 operator instead (the caller reloads its
 // populations in the second case: every scheme's step reads and writes a
-// cell's slots from the same thread, so they are still in memory).  Both paths compute the update of Section 2.6 to
-// within a few FP64 rounding errors; which one a cell takes depends only on
-// its own populations, so every scheme (they differ only in where they load
-// and store) still produces bit-identical results.
+// cell's slots from the same thread, so they are still in memory).  Both
+// paths compute the update of Section 2.6 to within a few FP64 rounding
+// errors; which one a cell takes depends only on its own populations, so every
+// scheme (they differ only in where they load and store) still produces
+// bit-identical results.
 #pragma once
 #include <cstring>
 
