@@ -378,7 +378,7 @@ __device__ __forceinline__ void collide_cell(typename Store<P>::R (&f)[Q], const
     if (st == FX_DONE) return;
     if (st == FX_REDO) reload(f);
   }
-  collide<Q, M, R, Store<P>::shifted>(f, cp, cs);
+  collide<Q, M, R, Store<P>::shifted, P == F32>(f, cp, cs);
 }
 
 // rate_fn() yields the relaxation rates; it is called just before the
