@@ -16,7 +16,9 @@
  *   2. for every direction k:   if x + c_k is fluid, f_k(x + c_k) <- f_out_k(x)
  *                               else  f_kbar(x) <- f_out_k(x) - 6 t_k rho_w c_k.u_w
  *      (link-wise bounce-back with momentum exchange, Section 2.1, rho_w = 1)
- *   into a fresh array, with periodic wrap at the domain faces.
+ *   into a fresh array, with periodic wrap at the domain faces.  orc_step_curved
+ *   places walls at a fraction of their links (the curved-wall extension of
+ *   link-wise bounce-back the paper points to in Section 1; see there).
  * Solid cells hold zeros.  Every scheme and layout of the paper computes this
  * same map (end of Section 2.3), so the oracle implements only this plain
  * two-array form.
@@ -61,7 +63,10 @@
  * equal rates; cumulants against log-moment-generating-function derivatives;
  * Couette and TRT Poiseuille exactness, Taylor-Green decay and its order of
  * convergence; hand-enumerated pulls on tiny lattices; traversal-order
- * independence.  No function here is parity unpinned.
+ * independence; walls at a fraction of their links (orc_step_curved): the
+ * halfway case equal to the plain step bit for bit, Couette flow between
+ * off-lattice walls exact, Poiseuille flow second-order convergent.  No
+ * function here is parity unpinned.
  *
  * Compile with -ffp-contract=off so that each operation rounds once.
  */
@@ -666,9 +671,39 @@ static inline int64_t wrapi(int64_t a, int64_t n) { a %= n; return a < 0 ? a + n
  *        paper's method).
  * perm: NULL (natural order) or a permutation of 0..N-1 giving the traversal
  *       order; nthreads > 1 parallelises the natural-order traversal. */
+static int step_impl(int Q, int nx, int ny, int nz, const uint8_t* flags, const double* wall_u, int model,
+                     const double* params, const double* force, const int64_t* perm, int nthreads,
+                     const double* qfrac, const double* f, double* fnew);
+
 EXPORT int orc_step(int Q, int nx, int ny, int nz, const uint8_t* flags, const double* wall_u, int model,
                     const double* params, const double* force, const int64_t* perm, int nthreads,
                     const double* f, double* fnew) {
+    return step_impl(Q, nx, ny, nz, flags, wall_u, model, params, force, perm, nthreads, NULL, f, fnew);
+}
+
+/* The same iteration with walls at a fraction of their links (the extension to
+ * curved boundaries the paper points to in Section 1: link-wise and entirely
+ * local).  qfrac [Q][N]: for a fluid cell x and a link k whose neighbour x + c_k
+ * is solid, q = qfrac[k*N + i] in (0, 1] is the fraction of the link from x at
+ * which the wall lies; other entries are ignored.  The reflected population is
+ * the linear interpolation of Bouzidi, Firdaouss & Lallemand (2001), with
+ * W = -6 t_k rho_w c_k.u_w:
+ *   q >= 1/2:  f_kbar(x, t+1) = [f_out_k(x) + W] / (2q) + (2q - 1)/(2q) f_out_kbar(x)
+ *   q <  1/2:  f_kbar(x, t+1) = 2q f_out_k(x) + (1 - 2q) f_k(x, t) + W
+ * In the second form, f_k(x, t) -- the population that streamed into x from
+ * x - c_k -- stands for that neighbour's post-collision f_out_k(x - c_k), so that
+ * the rule stays local to x (it is the same value one step earlier, and equal to
+ * it in a steady flow).  q = 1/2 gives the halfway bounce-back exactly.  force:
+ * as in orc_step. */
+EXPORT int orc_step_curved(int Q, int nx, int ny, int nz, const uint8_t* flags, const double* wall_u, int model,
+                           const double* params, const double* force, const double* qfrac, int nthreads,
+                           const double* f, double* fnew) {
+    return step_impl(Q, nx, ny, nz, flags, wall_u, model, params, force, NULL, nthreads, qfrac, f, fnew);
+}
+
+static int step_impl(int Q, int nx, int ny, int nz, const uint8_t* flags, const double* wall_u, int model,
+                     const double* params, const double* force, const int64_t* perm, int nthreads,
+                     const double* qfrac, const double* f, double* fnew) {
     const lat_t* L = get_lat(Q);
     if (!L || nx < 1 || ny < 1 || nz < 1 || model < 0 || model >= M_COUNT) return -1;
     if (model == M_RR || model == M_K) get_parts(L);
@@ -700,7 +735,16 @@ EXPORT int orc_step(int Q, int nx, int ny, int nz, const uint8_t* flags, const d
             } else {
                 const double* uw = wall_u + 3 * fl;
                 double cu = L->c[k][0] * uw[0] + L->c[k][1] * uw[1] + L->c[k][2] * uw[2];
-                fnew[(int64_t)L->opp[k] * N + i] = fo[k] - 6.0 * L->t[k] * 1.0 * cu;
+                double W = -6.0 * L->t[k] * 1.0 * cu;
+                double v = fo[k] + W;
+                if (qfrac) {
+                    double q = qfrac[(int64_t)k * N + i];
+                    if (q >= 0.5)
+                        v = (fo[k] + W) / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * fo[L->opp[k]];
+                    else
+                        v = 2.0 * q * fo[k] + (1.0 - 2.0 * q) * fc[k] + W;
+                }
+                fnew[(int64_t)L->opp[k] * N + i] = v;
             }
         }
     }

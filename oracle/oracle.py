@@ -34,6 +34,7 @@ def lib():
         L.orc_cumulants.argtypes = [ctypes.c_int, dp, dp]
         L.orc_step.argtypes = [ctypes.c_int] * 4 + [u8p, dp, ctypes.c_int, dp, dp, i64p, ctypes.c_int, dp, dp]
         L.orc_run.argtypes = [ctypes.c_int] * 4 + [u8p, dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, dp]
+        L.orc_step_curved.argtypes = [ctypes.c_int] * 4 + [u8p, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int, dp, dp]
         L.orc_macroscopic.argtypes = [ctypes.c_int, ctypes.c_int64, u8p, dp, dp, dp, dp]
         L.orc_conserved.argtypes = [ctypes.c_int, ctypes.c_int64, u8p, dp, dp, dp]
         L.orc_init_equilibrium_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, u8p, dp, dp, dp]
@@ -122,6 +123,8 @@ class Lattice:
         self.prm = _c64(prm)
         self.wall_u = _c64(wall_table(wall_velocities))
         self.f = np.zeros((Q, self.N))
+        # walls at a fraction of their links: [Q][N] (see orc_step_curved), or None (halfway)
+        self.qfrac = None
 
     def init_equilibrium(self, rho=None, u=None):
         """f = the model's own equilibrium of per-cell rho[N], u[3][N] (None: rho = 1, u = 0);
@@ -141,6 +144,17 @@ class Lattice:
         L = lib()
         fl = self.flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
         fp = None if force is None else _dp(_c64(force))
+        if self.qfrac is not None:
+            if perm is not None:
+                raise ValueError("traversal permutations are not combined with curved walls")
+            q = np.ascontiguousarray(np.asarray(self.qfrac, dtype=np.float64).reshape(self.Q, self.N))
+            for _ in range(n):
+                new = np.zeros_like(self.f)
+                _check(L.orc_step_curved(self.Q, self.nx, self.ny, self.nz, fl, _dp(self.wall_u),
+                                         MODELS[self.model], _dp(self.prm), fp, _dp(q), nthreads, _dp(self.f),
+                                         _dp(new)), "step_curved")
+                self.f = new
+            return
         if perm is None and n > 1:
             _check(L.orc_run(self.Q, self.nx, self.ny, self.nz, fl, _dp(self.wall_u), MODELS[self.model],
                              _dp(self.prm), fp, n, nthreads, _dp(self.f)), "run")
