@@ -142,6 +142,26 @@ LBM_API int lbm_set_precision(lbm_t h, int precision);
  * next step. */
 LBM_API int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, double uz);
 
+/* Walls at a fraction of their links: the extension of link-wise bounce-back
+ * to curved walls that Section 1 points to, kept local to the wall cell.
+ * q: host, FP64 [Q][N] canonical; for every fluid cell i and link k whose
+ * neighbour x + c_k is solid, q[k*N + i] in (0, 1] is the fraction of the
+ * link from x at which the wall lies (1/2: the halfway bounce-back of Section
+ * 2.1); entries of other links are ignored.  The reflected population of a
+ * link with q != 1/2 is the linear interpolation of Bouzidi, Firdaouss &
+ * Lallemand (2001), W being the link's wall term -6 t_k rho_w c_k.u_w:
+ *   q >= 1/2:  f_kbar(x, t+1) = [f_out_k(x) + W] / (2q) + (2q - 1)/(2q) f_out_kbar(x)
+ *   q <  1/2:  f_kbar(x, t+1) = 2q f_out_k(x) + (1 - 2q) f_k(x, t) + W
+ * with the cell's pre-collision f_k(x, t) standing for the neighbour's
+ * post-collision f_out_k(x - c_k) (the same value one step earlier).  The
+ * array is copied; the library keeps a per-cell index (4 bytes per cell) and
+ * the Q fractions of each cell with a link at q != 1/2, counted by
+ * lbm_device_bytes.  q NULL removes them (halfway walls again).  Takes effect
+ * at the next step; waits for the handle's stream.  LBM_ERR_INVALID_ARG for a
+ * NULL handle or a fraction outside (0, 1] on a wall link; a handle with such
+ * walls cannot join a batch (LBM_ERR_UNSUPPORTED from lbm_batch_add). */
+LBM_API int lbm_set_link_fractions(lbm_t h, const double* q);
+
 /* Set LBM_PARAM_*.  omega and omega_bulk in (0, 2), omega_high in (0, 2],
  * lambda > 0, wait_cycles an integer in [1, 2^40].  Takes effect at the next
  * step. */

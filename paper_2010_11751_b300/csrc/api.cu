@@ -77,6 +77,7 @@ int resolve_kernels(lbm_s* h) {
   h->sfns[0] = staged ? staged_fn(h->model, h->Q, h->prec, K_AA_EVEN) : nullptr;
   h->sfns[1] = staged ? staged_fn(h->model, h->Q, h->prec, K_AA_ODD) : nullptr;
   for (int sk = 0; sk < NUM_STEP_KINDS; ++sk) h->sumfns[sk] = step_sum_fn(h->model, h->Q, h->prec, h->layout, sk);
+  for (int sk = 0; sk < NUM_STEP_KINDS; ++sk) h->cfns[sk] = curved_fn(h->model, h->Q, h->prec, h->layout, sk);
   return LBM_OK;
 }
 
@@ -181,6 +182,8 @@ KArgs make_args(const lbm_s* h) {
   a.flags = h->d_flags;
   a.nbmask = h->d_nbmask;
   a.wall = h->d_wall;
+  a.qidx = h->d_qidx;
+  a.qtab = h->d_qtab;
   a.nx = h->nx;
   a.ny = h->ny;
   a.nz = h->nz;
@@ -395,6 +398,80 @@ int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, double uz) {
   return LBM_OK;
 }
 
+int lbm_set_link_fractions(lbm_t h, const double* q) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  const int Q = h->Q, N = h->N;
+  std::vector<int> qidx, cells;
+  std::vector<double> rows;
+  if (q) {
+    // the classified flag bytes: wall kind in bits 0..2
+    std::vector<uint8_t> fl((size_t)N);
+    LBM_CUDA(cudaMemcpyAsync(fl.data(), h->d_flags, (size_t)N, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    int cv[27][3];
+    for (int k = 0; k < Q; ++k)
+      for (int d = 0; d < 3; ++d) cv[k][d] = Q == 19 ? Lat<19>::c(k, d) : Lat<27>::c(k, d);
+    qidx.assign((size_t)N, -1);
+    cells.clear();
+    const int sxy = h->ny * h->nz;
+    for (int i = 0; i < N; ++i) {
+      if (fl[(size_t)i] & FLAG_KIND) continue;
+      const int x = i / sxy, y = (i / h->nz) % h->ny, z = i % h->nz;
+      bool curved = false;
+      for (int k = 0; k < Q; ++k) {
+        const int xn = (x + cv[k][0] + h->nx) % h->nx, yn = (y + cv[k][1] + h->ny) % h->ny,
+                  zn = (z + cv[k][2] + h->nz) % h->nz;
+        if (!(fl[(size_t)((xn * h->ny + yn) * h->nz + zn)] & FLAG_KIND)) continue;
+        const double v = q[(size_t)k * N + i];
+        if (!(v > 0.0 && v <= 1.0))
+          return fail(LBM_ERR_INVALID_ARG, "link fraction of cell " + std::to_string(i) + ", link " +
+                                               std::to_string(k) + " is not in (0, 1]");
+        if (v != 0.5) curved = true;
+      }
+      if (!curved) continue;
+      qidx[(size_t)i] = (int)(rows.size() / Q);
+      cells.push_back(i);
+      for (int k = 0; k < Q; ++k) rows.push_back(q[(size_t)k * N + i]);
+    }
+  }
+  // replace the tables (the previous steps must be done with them)
+  const bool had = h->nqcells > 0;
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->d_qidx) LBM_CUDA(cudaFree(h->d_qidx));
+  if (h->d_qtab) LBM_CUDA(cudaFree(h->d_qtab));
+  if (h->d_qcells) LBM_CUDA(cudaFree(h->d_qcells));
+  h->d_qidx = nullptr;
+  h->d_qtab = nullptr;
+  h->d_qcells = nullptr;
+  h->qrows = 0;
+  h->nqcells = 0;
+  if (!rows.empty()) {
+    LBM_CUDA(cudaMalloc(&h->d_qidx, sizeof(int) * (size_t)N));
+    LBM_CUDA(cudaMalloc(&h->d_qtab, sizeof(double) * rows.size()));
+    LBM_CUDA(cudaMalloc(&h->d_qcells, sizeof(int) * cells.size()));
+    LBM_CUDA(cudaMemcpyAsync(h->d_qidx, qidx.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(h->d_qtab, rows.data(), sizeof(double) * rows.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    LBM_CUDA(cudaMemcpyAsync(h->d_qcells, cells.data(), sizeof(int) * cells.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    h->qrows = (int)(rows.size() / Q);
+    h->nqcells = (int)cells.size();
+  }
+  LBM_CUDA(launch_mark_curved(h->d_nbmask, h->d_qidx, N, h->stream));
+  // the listed-cell records carry the mark: build them again at the next staged step
+  if (h->nlist >= 0 && (had || h->nqcells > 0)) {
+    if (h->d_list) LBM_CUDA(cudaFree(h->d_list));
+    if (h->d_list_mask) LBM_CUDA(cudaFree(h->d_list_mask));
+    if (h->d_list_kinds) LBM_CUDA(cudaFree(h->d_list_kinds));
+    h->d_list = nullptr;
+    h->d_list_mask = nullptr;
+    h->d_list_kinds = nullptr;
+    h->nlist = -1;
+  }
+  LBM_CUDA(cudaStreamSynchronize(h->stream));  // the host tables above are freed on return
+  return LBM_OK;
+}
+
 int lbm_set_param(lbm_t h, int key, double v) {
   if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
   switch (key) {
@@ -492,7 +569,9 @@ int step_sum_parts(lbm_s* h, int* nparts) {
     else if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
     return LBM_OK;
   }
-  if (h->sumfns[next_step_kind(h)]) *nparts = sum_blocks(h);
+  // the summing step kernels leave the cells with walls at a fraction of their
+  // links (and their sums) to the curved-cell kernel: reduce separately then
+  if (h->sumfns[next_step_kind(h)] && h->nqcells == 0) *nparts = sum_blocks(h);
   return LBM_OK;
 }
 
@@ -503,11 +582,16 @@ int enqueue_step(lbm_s* h, double* sum_partials = nullptr, int* nparts = nullptr
   KArgs a = make_args(h);
   cudaError_t e = cudaSuccess;
   auto kernel = [&](int sk) {
+    cudaError_t r;
     if (sum_partials) {
       *nparts = sum_blocks(h);
-      return h->sumfns[sk](a, h->threads, sum_partials, h->stream);
+      r = h->sumfns[sk](a, h->threads, sum_partials, h->stream);
+    } else {
+      r = h->fns[sk](a, h->threads, h->stream);
     }
-    return h->fns[sk](a, h->threads, h->stream);
+    // the cells with walls at a fraction of their links, which the step kernel left alone
+    if (r == cudaSuccess && h->nqcells > 0) r = h->cfns[sk](a, h->d_qcells, h->nqcells, h->stream);
+    return r;
   };
   switch (h->scheme) {
     case LBM_TWOPOP:
@@ -699,7 +783,8 @@ int lbm_device_bytes(lbm_t h, size_t* bytes) {
   size_t b = (size_t)h->N * (1 + sizeof(uint32_t)) + STAGE_PAD_BYTES +
              sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2 + h->sum_partials_cap) + h->stage_bytes +
              2 * sizeof(int) +
-             (h->nlist > 0 ? (sizeof(int) + sizeof(uint32_t) + 2 * sizeof(unsigned long long)) * (size_t)h->nlist : 0);
+             (h->nlist > 0 ? (sizeof(int) + sizeof(uint32_t) + 2 * sizeof(unsigned long long)) * (size_t)h->nlist : 0) +
+             (h->d_qidx ? sizeof(int) * ((size_t)h->N + h->nqcells) + sizeof(double) * (size_t)h->qrows * h->Q : 0);
   for (int a = 0; a < 2; ++a)
     if (h->d_pop[a]) b += pop_bytes(h) + STAGE_PAD_BYTES;
   *bytes = b;
@@ -753,6 +838,9 @@ int lbm_destroy(lbm_t h) {
   if (h->d_tile_off) cudaFree(h->d_tile_off);
   if (h->d_list_mask) cudaFree(h->d_list_mask);
   if (h->d_list_kinds) cudaFree(h->d_list_kinds);
+  if (h->d_qidx) cudaFree(h->d_qidx);
+  if (h->d_qtab) cudaFree(h->d_qtab);
+  if (h->d_qcells) cudaFree(h->d_qcells);
   delete h;
   return LBM_OK;
 }

@@ -237,6 +237,7 @@ int lbm_batch_add(lbm_batch_t b, lbm_t h) {
     return bfail(LBM_ERR_INVALID_ARG, "batch members must use the AA pattern and the SoA layout");
   if (std::find(b->members.begin(), b->members.end(), h) != b->members.end())
     return bfail(LBM_ERR_INVALID_ARG, "handle is already in the batch");
+  if (h->d_qidx) return bfail(LBM_ERR_UNSUPPORTED, "batch members cannot have walls at a fraction of their links");
   if (!b->members.empty() && (h->Q != b->Q || h->model != b->model || h->prec != b->prec))
     return bfail(LBM_ERR_INVALID_ARG, "batch members must share lattice, collision model and precision");
   if (b->members.empty()) {

@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   a.nz = mm->nz;
   a.N = mm->N;
   a.parity = SK == K_AA_ODD ? 1 : 0;
+  a.qidx = nullptr;  // members never have walls at a fraction of their links
+  a.qtab = nullptr;
   using R = typename Store<P>::R;
   // the member's rates, staged in shared memory once per block and read
   // from there just before each collision

@@ -44,6 +44,14 @@ struct lbm_s {
   int* d_tile_off = nullptr;   // per-tile offsets, only while the list is built
   int nlist = -1;              // number of listed cells; -1 until the list is built
   lbm::SideStream side;        // for the staged steps' listed-cell kernel
+  // walls at a fraction of their links (lbm_set_link_fractions): per cell its row
+  // of d_qtab ([rows][Q] link fractions) or -1; both null when there are none
+  int* d_qidx = nullptr;
+  double* d_qtab = nullptr;
+  int qrows = 0;
+  int* d_qcells = nullptr;  // those cells, updated by the curved-cell kernel after each step kernel
+  int nqcells = 0;
+  lbm::CurvedFn cfns[lbm::NUM_STEP_KINDS] = {};
 };
 
 namespace lbm {

@@ -22,7 +22,7 @@ using BatchFn = cudaError_t (*)(const BatchArgs&, int sk, int blocks, int thread
 // the fluid cells that are not bulk cells (flag byte non-zero), sorted, with a
 // record each: solid-neighbour mask | domain-face bit << 31, and the wall kind
 // of every solid neighbour (3 bits per link; links 0..20 in kinds[2t], 21..26
-// in kinds[2t + 1])
+// in kinds[2t + 1], whose bit 63 marks walls at a fraction of their links)
 struct Listed {
   const int* cell = nullptr;
   const uint32_t* mask = nullptr;
@@ -48,6 +48,10 @@ using StagedFn = cudaError_t (*)(const KArgs&, int* err, long long wait_cycles, 
 
 // step kernel for (lattice, model, precision, layout, step kind); nullptr if not built
 StepFn step_fn(int model, int Q, int P, int L, int SK);
+// one step of the listed cells with walls at a fraction of their links, for the
+// same key (run after the step kernel, which leaves those cells alone)
+using CurvedFn = cudaError_t (*)(const KArgs&, const int* cells, int n, cudaStream_t);
+CurvedFn curved_fn(int model, int Q, int P, int L, int SK);
 // summing step kernel for the same key (SoA only); nullptr if not built
 StepSumFn step_sum_fn(int model, int Q, int P, int L, int SK);
 // batched AA kernel (SoA) for (lattice, model, precision); nullptr if not built
@@ -58,6 +62,9 @@ StagedFn staged_fn(int model, int Q, int P, int SK);
 
 cudaError_t launch_classify(int Q, const uint8_t* raw, uint8_t* out, uint32_t* mask, int nx, int ny, int nz,
                             cudaStream_t s);
+// set (qidx[i] >= 0) or clear the curved-wall bit of every cell's solid-neighbour
+// mask; qidx null clears all
+cudaError_t launch_mark_curved(uint32_t* mask, const int* qidx, int N, cudaStream_t s);
 cudaError_t launch_macro(int Q, int P, int L, int LD, const KArgs& a, double* rho, double* u, const double* wall_u,
                          cudaStream_t s);
 cudaError_t launch_get(int Q, int P, int L, int LD, const KArgs& a, double* out, cudaStream_t s);

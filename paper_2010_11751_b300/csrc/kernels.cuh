@@ -51,6 +51,10 @@ struct KArgs {
   // per weight class c = |c|^2: w t_c, 3 w t_c, 3 w- t_c; and (1 - w)/2, (1 - w-)/2
   double wt[4], wt3[4], wm3[4], hs, hd;
   DFK dk;  // the same rates as double-float pairs (derived_dfk)
+  // walls at a fraction of their links: per cell the row of qtab holding its Q
+  // link fractions (-1: none), or null when the lattice has no such walls
+  const int* qidx;
+  const double* qtab;
 };
 
 // rate constants derived from w and w- (on the host: the kernels' launch
@@ -129,6 +133,7 @@ struct Nb {
   int i, x, y, z;
   int nx, ny, nz, sxy;
   bool edge;
+  bool curved;  // some of the cell's walls sit at a fraction of their links (qidx / qtab)
   uint32_t mask;
   const uint8_t* flags;
   // neighbourhood of cell i_ from its flag byte (the solid-neighbour mask is
@@ -140,9 +145,12 @@ struct Nb {
     if constexpr (FAST) {
       edge = false;
       mask = 0u;
+      curved = false;
     } else {
       edge = (fl & FLAG_EDGE) != 0;
       mask = (fl & FLAG_NEARWALL) ? __ldg(a.nbmask + i) : 0u;
+      curved = (mask & NBMASK_CURVED) != 0u;
+      mask &= ~NBMASK_CURVED;
       if (edge) {
         x = i / sxy;
         const int r = i - x * sxy;
@@ -159,6 +167,7 @@ struct Nb {
     x = y = z = 0;
     edge = edge_;
     mask = mask_;
+    curved = false;
     if (edge) {
       x = i / sxy;
       const int r = i - x * sxy;
@@ -206,7 +215,9 @@ struct NbRec : Nb<false> {
   unsigned long long kinds0, kinds1;
   __device__ __forceinline__ NbRec(int i_, const KArgs& a, uint32_t mask_edge, unsigned long long k0,
                                    unsigned long long k1)
-      : Nb<false>(i_, a, (mask_edge >> 31) != 0u, mask_edge & 0x7fffffffu), kinds0(k0), kinds1(k1) {}
+      : Nb<false>(i_, a, (mask_edge >> 31) != 0u, mask_edge & 0x7fffffffu), kinds0(k0), kinds1(k1) {
+    curved = (k1 >> 63) != 0ull;
+  }
   template <int Q, int K>
   __device__ __forceinline__ int kind() const {
     if constexpr (K < 21) return (int)((kinds0 >> (3 * K)) & 7ull);
@@ -228,26 +239,30 @@ __host__ __device__ constexpr int et_slot(bool bounced) {
 // ---------------------------------------------------------------------------
 // canonical load: the pre-collision populations of cell i, for the state kind
 // ---------------------------------------------------------------------------
+// address of the canonical pre-collision population k of cell nb.i
+template <int Q, int L, int LD, int k, class NB>
+__device__ __forceinline__ size_t load_addr(const KArgs& a, const NB& nb) {
+  const int N = a.N;
+  constexpr int kb = Lat<Q>::opp(k);
+  if constexpr (LD == LD_LOCAL || k == Lat<Q>::REST) {
+    return paddr<Q, L>(k, nb.i, N);
+  } else if constexpr (LD == LD_AA_ODD) {
+    // f_k(x) = pop_kbar(x - c_k) if x - c_k fluid, else pop_k(x)
+    if (!nb.template solid<Q, kb>()) return paddr<Q, L>(kb, nb.template idx<Q, kb>(), N);
+    return paddr<Q, L>(k, nb.i, N);
+  } else {
+    constexpr int PAR = LD == LD_ET_EVEN ? 0 : 1;
+    const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
+    if (!nb.template solid<Q, kb>()) return paddr<Q, L>(et_slot<Q, k, PAR>(false), cell, N);
+    return paddr<Q, L>(et_slot<Q, k, PAR>(true), cell, N);
+  }
+}
+
 template <int Q, int P, int L, int LD, bool FAST, typename T, class NB>
 __device__ __forceinline__ void load_cell(const KArgs& a, const NB& nb, const void* pop, T (&f)[Q]) {
-  const int N = a.N;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    constexpr int kb = Lat<Q>::opp(k);
-    size_t ad;
-    if constexpr (LD == LD_LOCAL || k == Lat<Q>::REST) {
-      ad = paddr<Q, L>(k, nb.i, N);
-    } else if constexpr (LD == LD_AA_ODD) {
-      // f_k(x) = pop_kbar(x - c_k) if x - c_k fluid, else pop_k(x)
-      if (!nb.template solid<Q, kb>()) ad = paddr<Q, L>(kb, nb.template idx<Q, kb>(), N);
-      else ad = paddr<Q, L>(k, nb.i, N);
-    } else {
-      constexpr int PAR = LD == LD_ET_EVEN ? 0 : 1;
-      const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
-      if (!nb.template solid<Q, kb>()) ad = paddr<Q, L>(et_slot<Q, k, PAR>(false), cell, N);
-      else ad = paddr<Q, L>(et_slot<Q, k, PAR>(true), cell, N);
-    }
-    f[k] = T(ldp<P>(pop, ad));
+    f[k] = T(ldp<P>(pop, load_addr<Q, L, LD, k>(a, nb)));
   });
 }
 
@@ -289,8 +304,62 @@ __device__ __forceinline__ void step_load(const KArgs& a, int i, typename Store<
   }
 }
 
+// walls at a fraction q of their links (lbm_set_link_fractions): the reflected
+// population of such a link k is the linear interpolation of Bouzidi,
+// Firdaouss & Lallemand (2001), with W the link's wall term:
+//   q >= 1/2:  (f_out_k + W) / (2q) + (2q - 1)/(2q) f_out_kbar
+//   q <  1/2:  2q f_out_k + (1 - 2q) f_k + W
+// where f_k is the cell's pre-collision population k (the population that
+// streamed in from x - c_k, standing for that neighbour's post-collision value,
+// so that the rule stays local).  It is read again from the cell's load slot:
+// no store of the cell has happened yet.  The value replaces f[k], complete with
+// its wall term; the returned mask marks those links, whose store adds nothing.
+// Links at q = 1/2 keep the halfway bounce-back of the store.  Shifted storage
+// (f - t_k) works unchanged: the weights of each form sum to one.
 template <int Q, int P, int L, int SK, class NB>
-__device__ __forceinline__ void step_store_nb(const KArgs& a, const NB& nb, const typename Store<P>::R (&f)[Q]) {
+__device__ __forceinline__ uint32_t curved_links(const KArgs& a, const NB& nb, typename Store<P>::R (&f)[Q]) {
+  using R = typename Store<P>::R;
+  constexpr int H = Lat<Q>::H;
+  if (!nb.curved) return 0u;
+  const double* q = a.qtab + (size_t)__ldg(a.qidx + nb.i) * Q;
+  uint32_t done = 0u;
+  static_for<0, H>([&](auto kc) {
+    constexpr int km = decltype(kc)::value, kp = km + H + 1;
+    // both members first from the unmodified pair (a narrow gap bounces both)
+    R vm = f[km], vp = f[kp];
+    auto one = [&](auto Kc, R fo, R fo_opp, R& out) {
+      constexpr int K = decltype(Kc)::value;
+      if (!nb.template solid<Q, K>()) return;
+      const double qk = __ldg(q + K);
+      if (qk == 0.5) return;
+      const R W = R(__ldg(a.wall + nb.template kind<Q, K>() * Q + K));
+      const R tq = R(2.0 * qk);
+      if (qk >= 0.5) {
+        out = (fo + W) / tq + ((tq - R(1)) / tq) * fo_opp;
+      } else {
+        R fin;
+        if constexpr (SK == K_ESOTWIST) {
+          fin = a.parity == 0 ? ldp<P>(a.a, load_addr<Q, L, LD_ET_EVEN, K>(a, nb))
+                              : ldp<P>(a.a, load_addr<Q, L, LD_ET_ODD, K>(a, nb));
+        } else {
+          constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : LD_LOCAL;
+          fin = ldp<P>(a.a, load_addr<Q, L, LD, K>(a, nb));
+        }
+        out = tq * fo + (R(1) - tq) * fin + W;
+      }
+      done |= 1u << K;
+    };
+    one(std::integral_constant<int, km>{}, f[km], f[kp], vm);
+    one(std::integral_constant<int, kp>{}, f[kp], f[km], vp);
+    f[km] = vm;
+    f[kp] = vp;
+  });
+  return done;
+}
+
+template <int Q, int P, int L, int SK, class NB>
+__device__ __forceinline__ void step_store_nb(const KArgs& a, const NB& nb, const typename Store<P>::R (&f)[Q],
+                                              uint32_t done = 0u) {
   using R = typename Store<P>::R;
   const int i = nb.i;
   const int N = a.N;
@@ -303,7 +372,7 @@ __device__ __forceinline__ void step_store_nb(const KArgs& a, const NB& nb, cons
     } else {
       const bool bounce = nb.template solid<Q, k>();
       R v = f[k];
-      if (bounce) v = v + R(__ldg(a.wall + nb.template kind<Q, k>() * Q + k));
+      if (bounce && !((done >> k) & 1u)) v = v + R(__ldg(a.wall + nb.template kind<Q, k>() * Q + k));
       if constexpr (SK == K_TWOPOP) {
         if (!bounce) stp<P>(a.b, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
         else stp<P>(a.b, paddr<Q, L>(kb, i, N), v);
@@ -381,6 +450,13 @@ __device__ __forceinline__ void collide_cell(typename Store<P>::R (&f)[Q], const
   collide<Q, M, R, Store<P>::shifted, P == F32>(f, cp, cs);
 }
 
+// the cells with walls at a fraction of their links are updated by
+// curved_cells_kernel, after the step kernel (the cells of one step touch
+// disjoint memory, so which launch updates a cell does not matter)
+__device__ __forceinline__ bool curved_cell(const KArgs& a, int i, uint8_t fl) {
+  return a.qidx != nullptr && (fl & FLAG_NEARWALL) && (__ldg(a.nbmask + i) & NBMASK_CURVED);
+}
+
 // rate_fn() yields the relaxation rates; it is called just before the
 // collision, so that a single-lattice kernel reads them from its launch
 // parameters without holding registers across the loads
@@ -397,12 +473,19 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
     if (in_range) step_load<Q, P, L, SK, true>(a, i, f);
     fl = a.flags[i];
     if (fl & FLAG_KIND) return;  // solid cell: nothing to update
-    if (fl != 0) step_load<Q, P, L, SK, false>(a, i, f, fl);
+    if (fl != 0) {
+      if (curved_cell(a, i, fl)) return;
+      step_load<Q, P, L, SK, false>(a, i, f, fl);
+    }
   } else {
     fl = a.flags[i];
     if (fl & FLAG_KIND) return;
-    if (fl == 0) step_load<Q, P, L, SK, true>(a, i, f);
-    else step_load<Q, P, L, SK, false>(a, i, f, fl);
+    if (fl == 0) {
+      step_load<Q, P, L, SK, true>(a, i, f);
+    } else {
+      if (curved_cell(a, i, fl)) return;
+      step_load<Q, P, L, SK, false>(a, i, f, fl);
+    }
   }
   const CP<R> cp = rate_fn();
   // (a reload reads the cell's slots again: every scheme's step reads and
@@ -414,6 +497,7 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
   if (fl == 0) step_store<Q, P, L, SK, true>(a, i, f);
   else step_store<Q, P, L, SK, false>(a, i, f, fl);
 }
+
 
 // FP32/FP16 kernels of the light models are bound by memory latency: capping
 // registers so that six (D3Q19) or four (D3Q27) 256-thread blocks fit per SM
@@ -533,6 +617,67 @@ cudaError_t launch_step(const KArgs& a, int threads, cudaStream_t s) {
   const int blocks = (a.N + threads - 1) / threads;
   step_kernel<Q, M, P, L, SK><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+// one step of the cells with walls at a fraction of their links (a list of n
+// cells), one thread each: load, collide, the interpolated reflections
+// (curved_links), store
+template <int Q, int M, int P, int L, int SK>
+__global__ void __launch_bounds__(128) curved_cells_kernel(KArgs a, const int* cells, int n) {
+  using R = typename Store<P>::R;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = __ldg(cells + t);
+  const uint8_t fl = a.flags[i];
+  const Nb<false> nb(i, a, fl);
+  R f[Q];
+  auto load = [&](R (&g)[Q]) {
+    if constexpr (SK == K_ESOTWIST) {
+      if (a.parity == 0) load_cell<Q, P, L, LD_ET_EVEN, false>(a, nb, a.a, g);
+      else load_cell<Q, P, L, LD_ET_ODD, false>(a, nb, a.a, g);
+    } else {
+      load_cell<Q, P, L, SK == K_AA_ODD ? LD_AA_ODD : LD_LOCAL, false>(a, nb, a.a, g);
+    }
+  };
+  load(f);
+  collide_cell<Q, M, P>(f, rates<P>(a), nullptr, load);
+  const uint32_t done = curved_links<Q, P, L, SK>(a, nb, f);
+  step_store_nb<Q, P, L, SK>(a, nb, f, done);
+}
+
+template <int Q, int M, int P, int L, int SK>
+cudaError_t launch_curved(const KArgs& a, const int* cells, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  curved_cells_kernel<Q, M, P, L, SK><<<(n + 127) / 128, 128, 0, s>>>(a, cells, n);
+  return cudaGetLastError();
+}
+
+using CurvedFn = cudaError_t (*)(const KArgs&, const int* cells, int n, cudaStream_t);
+
+// one model: all lattices, storages, layouts and step kinds
+template <int M>
+CurvedFn curved_fn_for_model(int Q, int P, int L, int SK) {
+#define LBM_CK(QQ, PP, LL)                                          \
+  switch (SK) {                                                     \
+    case K_TWOPOP: return &launch_curved<QQ, M, PP, LL, K_TWOPOP>;   \
+    case K_AA_EVEN: return &launch_curved<QQ, M, PP, LL, K_AA_EVEN>; \
+    case K_AA_ODD: return &launch_curved<QQ, M, PP, LL, K_AA_ODD>;   \
+    case K_ESOTWIST: return &launch_curved<QQ, M, PP, LL, K_ESOTWIST>; \
+    default: return nullptr;                                        \
+  }
+  if (Q == 19) {
+    if (P == F64 && L == SOA) { LBM_CK(19, F64, SOA) }
+    if (P == F64 && L == AOS) { LBM_CK(19, F64, AOS) }
+    if (P == F32 && L == SOA) { LBM_CK(19, F32, SOA) }
+    if (P == F16 && L == SOA) { LBM_CK(19, F16, SOA) }
+  } else if (Q == 27) {
+    if (P == F64 && L == SOA) { LBM_CK(27, F64, SOA) }
+    if (P == F64 && L == AOS) { LBM_CK(27, F64, AOS) }
+    if (P == F32 && L == SOA) { LBM_CK(27, F32, SOA) }
+    if (P == F16 && L == SOA) { LBM_CK(27, F16, SOA) }
+  }
+#undef LBM_CK
+  return nullptr;
 }
 
 // one model: all lattices, storages, layouts and step kinds

@@ -136,5 +136,9 @@ constexpr uint8_t FLAG_NEARWALL = 0x80;
 // set when every solid neighbour has the same wall kind, stored in bits 27..29
 constexpr uint32_t NBMASK_UNIFORM = 1u << 30;
 constexpr int NBMASK_KIND_SHIFT = 27;
+// bit 31: some of the cell's walls sit at a fraction of their links
+// (lbm_set_link_fractions); in the listed-cell records it is bit 63 of the
+// second wall-kind word
+constexpr uint32_t NBMASK_CURVED = 1u << 31;
 
 }  // namespace lbm

@@ -11,4 +11,5 @@ StepFn step_fn_chm(int Q, int P, int L, int SK) { return step_fn_for_model<CHM>(
 BatchFn batch_fn_chm(int Q, int P) { return batch_fn_for_model<CHM>(Q, P); }
 StagedFn staged_fn_chm(int Q, int P, int SK) { return staged_fn_for_model<CHM>(Q, P, SK); }
 StepSumFn step_sum_fn_chm(int Q, int P, int L, int SK) { return step_sum_fn_for_model<CHM>(Q, P, L, SK); }
+CurvedFn curved_fn_chm(int Q, int P, int L, int SK) { return curved_fn_for_model<CHM>(Q, P, L, SK); }
 }  // namespace lbm

@@ -11,4 +11,5 @@ StepFn step_fn_hm(int Q, int P, int L, int SK) { return step_fn_for_model<HM>(Q,
 BatchFn batch_fn_hm(int Q, int P) { return batch_fn_for_model<HM>(Q, P); }
 StagedFn staged_fn_hm(int Q, int P, int SK) { return staged_fn_for_model<HM>(Q, P, SK); }
 StepSumFn step_sum_fn_hm(int Q, int P, int L, int SK) { return step_sum_fn_for_model<HM>(Q, P, L, SK); }
+CurvedFn curved_fn_hm(int Q, int P, int L, int SK) { return curved_fn_for_model<HM>(Q, P, L, SK); }
 }  // namespace lbm

@@ -11,4 +11,5 @@ StepFn step_fn_reg(int Q, int P, int L, int SK) { return step_fn_for_model<REG>(
 BatchFn batch_fn_reg(int Q, int P) { return batch_fn_for_model<REG>(Q, P); }
 StagedFn staged_fn_reg(int Q, int P, int SK) { return staged_fn_for_model<REG>(Q, P, SK); }
 StepSumFn step_sum_fn_reg(int Q, int P, int L, int SK) { return step_sum_fn_for_model<REG>(Q, P, L, SK); }
+CurvedFn curved_fn_reg(int Q, int P, int L, int SK) { return curved_fn_for_model<REG>(Q, P, L, SK); }
 }  // namespace lbm

@@ -11,4 +11,5 @@ StepFn step_fn_rr(int Q, int P, int L, int SK) { return step_fn_for_model<RR>(Q,
 BatchFn batch_fn_rr(int Q, int P) { return batch_fn_for_model<RR>(Q, P); }
 StagedFn staged_fn_rr(int Q, int P, int SK) { return staged_fn_for_model<RR>(Q, P, SK); }
 StepSumFn step_sum_fn_rr(int Q, int P, int L, int SK) { return step_sum_fn_for_model<RR>(Q, P, L, SK); }
+CurvedFn curved_fn_rr(int Q, int P, int L, int SK) { return curved_fn_for_model<RR>(Q, P, L, SK); }
 }  // namespace lbm

@@ -11,4 +11,5 @@ StepFn step_fn_trt(int Q, int P, int L, int SK) { return step_fn_for_model<TRT>(
 BatchFn batch_fn_trt(int Q, int P) { return batch_fn_for_model<TRT>(Q, P); }
 StagedFn staged_fn_trt(int Q, int P, int SK) { return staged_fn_for_model<TRT>(Q, P, SK); }
 StepSumFn step_sum_fn_trt(int Q, int P, int L, int SK) { return step_sum_fn_for_model<TRT>(Q, P, L, SK); }
+CurvedFn curved_fn_trt(int Q, int P, int L, int SK) { return curved_fn_for_model<TRT>(Q, P, L, SK); }
 }  // namespace lbm

@@ -313,7 +313,8 @@ __global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed liste
     const CP<R> cp = rates<P>(a);
     collide_cell<Q, M, P>(f, cp, SUMS ? &cs : nullptr,
                           [&](R (&g)[Q]) { load_cell<Q, P, SOA, LD, false>(a, nb, a.a, g); });
-    step_store_nb<Q, P, SOA, SK>(a, nb, f);
+    const uint32_t done = curved_links<Q, P, SOA, SK>(a, nb, f);
+    step_store_nb<Q, P, SOA, SK>(a, nb, f, done);
   }
   if constexpr (SUMS) {
     double m = cs.rho, e = cs.ke;

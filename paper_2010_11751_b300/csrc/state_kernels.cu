@@ -448,7 +448,20 @@ __global__ void listed_records_kernel(KArgs a, const int* list, int n, uint32_t*
   });
   mask[t] = nb.mask | (nb.edge ? 0x80000000u : 0u);
   kinds[2 * (size_t)t] = k0;
-  kinds[2 * (size_t)t + 1] = k1;
+  kinds[2 * (size_t)t + 1] = k1 | (nb.curved ? (1ull << 63) : 0ull);
+}
+
+__global__ void mark_curved_kernel(uint32_t* mask, const int* qidx, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool on = qidx != nullptr && qidx[i] >= 0;
+  mask[i] = (mask[i] & ~NBMASK_CURVED) | (on ? NBMASK_CURVED : 0u);
+}
+
+cudaError_t launch_mark_curved(uint32_t* mask, const int* qidx, int N, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  mark_curved_kernel<<<(N + 255) / 256, 256, 0, s>>>(mask, qidx, N);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_listed_records(int Q, const KArgs& a, const int* list, int n, uint32_t* mask,

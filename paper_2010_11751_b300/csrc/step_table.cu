@@ -55,6 +55,19 @@ StagedFn staged_fn_k(int, int, int);
 StagedFn staged_fn_bgk_w2_loop(int, int, int);
 StagedFn staged_fn_bgk_w2_edu(int, int, int);
 
+CurvedFn curved_fn_bgk_nw4(int, int, int, int);
+CurvedFn curved_fn_bgk_w2(int, int, int, int);
+CurvedFn curved_fn_bgk_w2_edu(int, int, int, int);
+CurvedFn curved_fn_bgk_w2_loop(int, int, int, int);
+CurvedFn curved_fn_chm(int, int, int, int);
+CurvedFn curved_fn_cm(int, int, int, int);
+CurvedFn curved_fn_hm(int, int, int, int);
+CurvedFn curved_fn_k(int, int, int, int);
+CurvedFn curved_fn_reg(int, int, int, int);
+CurvedFn curved_fn_rm(int, int, int, int);
+CurvedFn curved_fn_rr(int, int, int, int);
+CurvedFn curved_fn_trt(int, int, int, int);
+
 StepFn step_fn(int model, int Q, int P, int L, int SK) {
   switch (model) {
     case BGK_W2: return step_fn_bgk_w2(Q, P, L, SK);
@@ -69,6 +82,24 @@ StepFn step_fn(int model, int Q, int P, int L, int SK) {
     case KUM: return step_fn_k(Q, P, L, SK);
     case BGK_W2_LOOP: return step_fn_bgk_w2_loop(Q, P, L, SK);
     case BGK_W2_EDU: return step_fn_bgk_w2_edu(Q, P, L, SK);
+    default: return nullptr;
+  }
+}
+
+CurvedFn curved_fn(int model, int Q, int P, int L, int SK) {
+  switch (model) {
+    case BGK_W2: return curved_fn_bgk_w2(Q, P, L, SK);
+    case BGK_NW4: return curved_fn_bgk_nw4(Q, P, L, SK);
+    case TRT: return curved_fn_trt(Q, P, L, SK);
+    case REG: return curved_fn_reg(Q, P, L, SK);
+    case RR: return curved_fn_rr(Q, P, L, SK);
+    case RM: return curved_fn_rm(Q, P, L, SK);
+    case HM: return curved_fn_hm(Q, P, L, SK);
+    case CM: return curved_fn_cm(Q, P, L, SK);
+    case CHM: return curved_fn_chm(Q, P, L, SK);
+    case KUM: return curved_fn_k(Q, P, L, SK);
+    case BGK_W2_LOOP: return curved_fn_bgk_w2_loop(Q, P, L, SK);
+    case BGK_W2_EDU: return curved_fn_bgk_w2_edu(Q, P, L, SK);
     default: return nullptr;
   }
 }

@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
         "lbm_set_layout": [vp, i],
         "lbm_set_precision": [vp, i],
         "lbm_set_wall_velocity": [vp, i, d, d, d],
+        "lbm_set_link_fractions": [vp, dp],
         "lbm_set_param": [vp, i, d],
         "lbm_set_stream": [vp, vp],
         "lbm_init_equilibrium": [vp, dp, dp],
@@ -132,6 +133,13 @@ def lbm_set_precision(h, precision):
 
 def lbm_set_wall_velocity(h, flag, ux, uy, uz):
     return _check(lib().lbm_set_wall_velocity(h, flag, ux, uy, uz))
+
+
+def lbm_set_link_fractions(h, q):
+    """q: None, or host FP64 [Q][N] wall fractions of the links that meet a wall."""
+    if q is not None:
+        q = np.ascontiguousarray(q, dtype=np.float64)
+    return _check(lib().lbm_set_link_fractions(h, ptr(q)))
 
 
 def lbm_set_param(h, key, value):
@@ -348,6 +356,14 @@ class Lattice:
 
     def reduce(self):
         return lbm_reduce(self.h)
+
+    def set_link_fractions(self, q):
+        """Walls at a fraction q of their links ([Q][N] FP64, or None for halfway walls)."""
+        if q is not None:
+            q = np.asarray(q, dtype=np.float64)
+            if q.size != self.Q * self.N:
+                raise LBMError(ERR_INVALID_ARG, f"link fractions need {self.Q} x {self.N} values")
+        lbm_set_link_fractions(self.h, q)
 
     def set_param(self, key, value):
         lbm_set_param(self.h, key, value)
