@@ -229,11 +229,33 @@ LBM_API int lbm_bytes_per_cell_update(lbm_t h, double* bytes);
 
 /* Number of kernel launches one time step of the handle makes (*n >= 1):
  * 1 for the one-thread-per-cell kernels; 2 for swap (collision, then the
- * streaming pass) and for the staged AA steps of FP16 SoA storage (the
- * shared-memory-staged kernel over the bulk cells, then the kernel over the
- * cells next to a wall or on a domain face, if there are any).  May build the
- * latter's cell list (device memory it owns; see lbm_device_bytes). */
+ * streaming pass) and for the staged AA steps of SoA storage in FP16 (every
+ * model) and in FP64 (BGK-W2 and TRT): the shared-memory-staged kernel over
+ * the bulk cells, then the kernel over the cells next to a wall or on a domain
+ * face, if there are any.  May build the latter's cell list (device memory it
+ * owns; see lbm_device_bytes). */
 LBM_API int lbm_kernels_per_step(lbm_t h, int* n);
+
+/* Bounds checks (no counterpart in the paper; a test and debugging aid).
+ * liblbm_debug.so, built from the same sources with -DLBM_DEBUG (collision
+ * models BGK-W2, TRT and K only), checks in every kernel each population load
+ * and store against the array's Q N populations, each own or neighbour cell
+ * index and flag / mask read against [0, N), each bulk copy of the staged
+ * steps against the array plus its 128 bytes of padding, and each read of a
+ * staged run against the run in shared memory.  A failed check records the
+ * handle's first fault and skips the access (a skipped load reads 0); nothing
+ * traps.  The padding past the population and flag arrays holds canary bytes
+ * (0xA5) in that build.
+ *   Synchronises the handle's streams, then *fault = 0 when no check failed
+ *   and every canary is intact; else kind << 56 | index: kind 1 population
+ *   load, 2 population store (index: element), 3 cell, 4 flag read, 5 mask
+ *   read (index: cell), 6 staged population copy, 7 staged flag copy (index:
+ *   end of the copy), 8 staged run read (index in the run), 9 link-fraction
+ *   row, 10 canary (array 0 / 1 populations, 2 flags, in bits 32..39; byte of
+ *   the padding below).  The device fault word is cleared by the read.
+ * liblbm.so has no checks: it sets *fault = 0 and returns
+ * LBM_ERR_UNSUPPORTED. */
+LBM_API int lbm_debug_check(lbm_t h, unsigned long long* fault);
 
 /* Free everything the handle owns.  NULL is accepted. */
 LBM_API int lbm_destroy(lbm_t h);

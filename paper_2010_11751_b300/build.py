@@ -4,6 +4,13 @@ Every translation unit under csrc/ is compiled by nvcc in parallel into
 _build/, then linked into paper_2010_11751_b300/liblbm.so with the CUDA runtime
 linked statically.  A rebuild happens when any source or header is newer than
 the library.
+
+build(debug=True) makes liblbm_debug.so instead: the same sources compiled
+with -DLBM_DEBUG into _build/debug/, whose kernels check every population,
+cell, flag and staged-copy index against the arrays' extents and record the
+first fault per handle instead of touching memory out of bounds
+(lbm_debug_check reads it).  It holds three collision models (BGK-W2, TRT and
+the cumulant model), which keeps its build short.
 """
 import concurrent.futures as cf
 import glob
@@ -18,6 +25,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
+LIB_DEBUG = os.path.join(PKG, "liblbm_debug.so")
+BUILD_DEBUG = os.path.join(BUILD, "debug")
+# the model translation units of the bounds-checked build
+DEBUG_MODELS = ("model_bgk_w2.cu", "model_trt.cu", "model_k.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -27,8 +38,12 @@ def _nvcc():
     return shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+def _sources(debug=False):
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    if debug:
+        srcs = [s for s in srcs if not os.path.basename(s).startswith("model_")
+                or os.path.basename(s) in DEBUG_MODELS]
+    return srcs
 
 
 def _inputs():
@@ -36,10 +51,11 @@ def _inputs():
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(debug=False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
@@ -48,9 +64,9 @@ def _headers():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _compile(src, extra, force=False):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    if not force and not extra and os.path.exists(obj):
+def _compile(src, extra, force=False, objdir=BUILD, reuse=True):
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+    if not force and reuse and os.path.exists(obj):
         t = os.path.getmtime(obj)
         if all(os.path.getmtime(p) <= t for p in [src, os.path.abspath(__file__)] + _headers()):
             return obj, ""
@@ -61,28 +77,32 @@ def _compile(src, extra, force=False):
     return obj, r.stderr
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = _sources()
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra=(), debug=False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(debug):
+        return lib
+    objdir = BUILD_DEBUG if debug else BUILD
+    os.makedirs(objdir, exist_ok=True)
+    srcs = _sources(debug)
     # heaviest units first so the parallel build finishes sooner
     srcs.sort(key=lambda s: ("model_k" not in s and "model_c" not in s and "model_rr" not in s, s))
     jobs = jobs or max(1, os.cpu_count() or 1)
+    flags = list(extra) + (["-DLBM_DEBUG"] if debug else [])
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra), force), srcs))
+        # objects are reused only by builds without extra nvcc flags
+        results = list(ex.map(lambda s: _compile(s, flags, force, objdir, reuse=not extra), srcs))
     if verbose:
         for _, err in results:
             if err:
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     t = build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-              extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [])
+              extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [], debug="--debug" in sys.argv)
     print(t)

@@ -146,6 +146,9 @@ int ensure_alloc(lbm_s* h) {
     // the staged kernels copy whole 128-byte units, up to STAGE_PAD_BYTES past the end
     LBM_CUDA(cudaMalloc(&h->d_pop[a], pop_bytes(h) + STAGE_PAD_BYTES));
     LBM_CUDA(cudaMemsetAsync(h->d_pop[a], 0, pop_bytes(h) + STAGE_PAD_BYTES, h->stream));
+    // bounds-checked build: the padding holds canary bytes that no kernel may write
+    LBM_IF_DEBUG(LBM_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(h->d_pop[a]) + pop_bytes(h), DEBUG_CANARY,
+                                          STAGE_PAD_BYTES, h->stream));)
   }
   return LBM_OK;
 }
@@ -175,6 +178,12 @@ int upload_wall(lbm_s* h) {
   return LBM_OK;
 }
 
+#ifdef LBM_DEBUG
+// the 64-bit fault word of the bounds-checked build (after the staged error
+// word and the scratch counter)
+unsigned long long* debug_word(const lbm_s* h) { return reinterpret_cast<unsigned long long*>(h->d_err + 2); }
+#endif
+
 KArgs make_args(const lbm_s* h) {
   KArgs a;
   a.a = h->d_pop[h->cur];
@@ -189,6 +198,11 @@ KArgs make_args(const lbm_s* h) {
   a.nz = h->nz;
   a.N = h->N;
   a.parity = (int)(h->steps & 1);
+#ifdef LBM_DEBUG
+  a.dbg = debug_word(h);
+  a.dbg_elems = (size_t)h->Q * (size_t)h->N;
+  a.dbg_qrows = h->qrows;
+#endif
   const double w = h->omega, wb = h->bulk_follows ? h->omega : h->omega_bulk;
   a.omega = w;
   a.omc = 1.0 - w;
@@ -333,8 +347,11 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
   uint8_t* raw = nullptr;
   cudaError_t e = cudaMalloc(&h->d_flags, N + STAGE_PAD_BYTES);  // padded as the populations
   if (e == cudaSuccess) e = cudaMemset(h->d_flags, 0, N + STAGE_PAD_BYTES);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 2 * sizeof(int));
+  LBM_IF_DEBUG(if (e == cudaSuccess) e = cudaMemset(h->d_flags + N, DEBUG_CANARY, STAGE_PAD_BYTES);)
+  // [0] staged-kernel error word, [1] scratch counter, [2..3] the 64-bit fault
+  // word of the bounds-checked build
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_nbmask, sizeof(uint32_t) * N);
   if (e == cudaSuccess) e = cudaMalloc(&raw, N);
   if (e == cudaSuccess) e = cudaMemcpy(raw, flags, N, cudaMemcpyHostToDevice);
@@ -782,7 +799,7 @@ int lbm_device_bytes(lbm_t h, size_t* bytes) {
   if (!h || !bytes) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
   size_t b = (size_t)h->N * (1 + sizeof(uint32_t)) + STAGE_PAD_BYTES +
              sizeof(double) * (8 * 27 + 24 + 2 * h->partials + 2 + h->sum_partials_cap) + h->stage_bytes +
-             2 * sizeof(int) +
+             4 * sizeof(int) +
              (h->nlist > 0 ? (sizeof(int) + sizeof(uint32_t) + 2 * sizeof(unsigned long long)) * (size_t)h->nlist : 0) +
              (h->d_qidx ? sizeof(int) * ((size_t)h->N + h->nqcells) + sizeof(double) * (size_t)h->qrows * h->Q : 0);
   for (int a = 0; a < 2; ++a)
@@ -812,6 +829,36 @@ int lbm_kernels_per_step(lbm_t h, int* n) {
   }
   *n = k;
   return LBM_OK;
+}
+
+int lbm_debug_check(lbm_t h, unsigned long long* fault) {
+  if (!h || !fault) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+#ifndef LBM_DEBUG
+  *fault = 0;
+  return fail(LBM_ERR_UNSUPPORTED, "this library is built without bounds checks; liblbm_debug.so has them");
+#else
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->side.side) LBM_CUDA(cudaStreamSynchronize(h->side.side));
+  unsigned long long w = 0;
+  LBM_CUDA(cudaMemcpy(&w, debug_word(h), sizeof(w), cudaMemcpyDeviceToHost));
+  if (w != 0) LBM_CUDA(cudaMemset(debug_word(h), 0, sizeof(w)));
+  // canaries of the padding past the population arrays (index 0, 1) and the flags (2)
+  unsigned char pad[STAGE_PAD_BYTES];
+  for (int a = 0; a < 3 && w == 0; ++a) {
+    const unsigned char* p = a < 2 ? (h->d_pop[a] ? static_cast<const unsigned char*>(h->d_pop[a]) + pop_bytes(h)
+                                                 : nullptr)
+                                   : h->d_flags + h->N;
+    if (!p) continue;
+    LBM_CUDA(cudaMemcpy(pad, p, STAGE_PAD_BYTES, cudaMemcpyDeviceToHost));
+    for (size_t b = 0; b < STAGE_PAD_BYTES; ++b)
+      if (pad[b] != DEBUG_CANARY) {
+        w = ((unsigned long long)DBG_PAD << 56) | ((unsigned long long)a << 32) | b;
+        break;
+      }
+  }
+  *fault = w;
+  return LBM_OK;
+#endif
 }
 
 int lbm_destroy(lbm_t h) {

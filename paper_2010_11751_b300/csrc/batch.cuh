@@ -27,6 +27,9 @@ struct __align__(16) Member {
   // parameters, so that no thread spends FP64 operations or conversions on them
   CP<double> rd;
   CP<float> rf;
+#ifdef LBM_DEBUG
+  unsigned long long* dbg;  // the member handle's fault word (debug.cuh)
+#endif
 };
 
 struct BatchArgs {
@@ -67,6 +70,11 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   a.parity = SK == K_AA_ODD ? 1 : 0;
   a.qidx = nullptr;  // members never have walls at a fraction of their links
   a.qtab = nullptr;
+#ifdef LBM_DEBUG
+  a.dbg = mm->dbg;
+  a.dbg_elems = (size_t)Q * (size_t)mm->N;
+  a.dbg_qrows = 0;
+#endif
   using R = typename Store<P>::R;
   // the member's rates, staged in shared memory once per block and read
   // from there just before each collision

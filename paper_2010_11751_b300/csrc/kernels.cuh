@@ -30,6 +30,7 @@
 #include <type_traits>
 
 #include "collision.cuh"
+#include "debug.cuh"
 
 namespace lbm {
 
@@ -55,6 +56,11 @@ struct KArgs {
   // link fractions (-1: none), or null when the lattice has no such walls
   const int* qidx;
   const double* qtab;
+#ifdef LBM_DEBUG
+  unsigned long long* dbg;  // first failed bounds check (debug.cuh)
+  size_t dbg_elems;         // populations in the array: Q N
+  int dbg_qrows;            // rows of qtab
+#endif
 };
 
 // rate constants derived from w and w- (on the host: the kernels' launch
@@ -103,23 +109,31 @@ inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4]
 // ---------------------------------------------------------------------------
 template <int Q, int L>
 __device__ __forceinline__ size_t paddr(int k, int i, int N) {
+  LBM_IF_DEBUG(if ((unsigned)i >= (unsigned)N || (unsigned)k >= (unsigned)Q) return DBG_BAD_ADDR;)
   if constexpr (L == SOA) return (size_t)k * (size_t)N + (size_t)i;
   else return (size_t)i * Q + (size_t)k;
 }
 
+// population load / store at element ad of the array at base (a: the step's
+// arguments, whose bounds the debug build checks)
 template <int P>
-__device__ __forceinline__ typename Store<P>::R ldp(const void* base, size_t a) {
+__device__ __forceinline__ typename Store<P>::R ldp(const KArgs& a, const void* base, size_t ad) {
   using S = typename Store<P>::S;
-  return Store<P>::to_r(__ldg(reinterpret_cast<const S*>(base) + a));
-}
-template <>
-__device__ __forceinline__ float ldp<F16>(const void* base, size_t a) {
-  return __half2float(reinterpret_cast<const __half*>(base)[a]);
+  LBM_IF_DEBUG(if (ad >= a.dbg_elems) {
+    dbg_fault(a.dbg, DBG_POP_LOAD, ad);
+    return typename Store<P>::R(0);
+  })
+  if constexpr (P == F16) return __half2float(reinterpret_cast<const __half*>(base)[ad]);
+  else return Store<P>::to_r(__ldg(reinterpret_cast<const S*>(base) + ad));
 }
 template <int P>
-__device__ __forceinline__ void stp(void* base, size_t a, typename Store<P>::R v) {
+__device__ __forceinline__ void stp(const KArgs& a, void* base, size_t ad, typename Store<P>::R v) {
   using S = typename Store<P>::S;
-  reinterpret_cast<S*>(base)[a] = Store<P>::from_r(v);
+  LBM_IF_DEBUG(if (ad >= a.dbg_elems) {
+    dbg_fault(a.dbg, DBG_POP_STORE, ad);
+    return;
+  })
+  reinterpret_cast<S*>(base)[ad] = Store<P>::from_r(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -136,10 +150,15 @@ struct Nb {
   bool curved;  // some of the cell's walls sit at a fraction of their links (qidx / qtab)
   uint32_t mask;
   const uint8_t* flags;
+#ifdef LBM_DEBUG
+  unsigned long long* dbg;
+  int ncell;
+#endif
   // neighbourhood of cell i_ from its flag byte (the solid-neighbour mask is
   // read from a.nbmask for cells next to a wall)
   __device__ __forceinline__ Nb(int i_, const KArgs& a, uint8_t fl = 0)
       : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
+    LBM_IF_DEBUG(dbg = a.dbg; ncell = a.N;)
     sxy = a.ny * a.nz;
     x = y = z = 0;
     if constexpr (FAST) {
@@ -148,6 +167,10 @@ struct Nb {
       curved = false;
     } else {
       edge = (fl & FLAG_EDGE) != 0;
+      LBM_IF_DEBUG(if ((fl & FLAG_NEARWALL) && (unsigned)i >= (unsigned)a.N) {
+        dbg_fault(a.dbg, DBG_MASK, (unsigned)i);
+        fl = 0;
+      })
       mask = (fl & FLAG_NEARWALL) ? __ldg(a.nbmask + i) : 0u;
       curved = (mask & NBMASK_CURVED) != 0u;
       mask &= ~NBMASK_CURVED;
@@ -163,6 +186,7 @@ struct Nb {
   __device__ __forceinline__ Nb(int i_, const KArgs& a, bool edge_, uint32_t mask_)
       : i(i_), nx(a.nx), ny(a.ny), nz(a.nz), flags(a.flags) {
     static_assert(!FAST, "bulk cells have neither solid neighbours nor wrap");
+    LBM_IF_DEBUG(dbg = a.dbg; ncell = a.N;)
     sxy = a.ny * a.nz;
     x = y = z = 0;
     edge = edge_;
@@ -200,7 +224,12 @@ struct Nb {
   template <int Q, int K>
   __device__ __forceinline__ int kind() const {
     if (mask & NBMASK_UNIFORM) return (int)((mask >> NBMASK_KIND_SHIFT) & FLAG_KIND);
-    return flags[at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>()] & FLAG_KIND;
+    const int j = at<Lat<Q>::c(K, 0), Lat<Q>::c(K, 1), Lat<Q>::c(K, 2)>();
+    LBM_IF_DEBUG(if ((unsigned)j >= (unsigned)ncell) {
+      dbg_fault(dbg, DBG_FLAG, (unsigned)j);
+      return 0;
+    })
+    return flags[j] & FLAG_KIND;
   }
   template <int Q, int K>
   __device__ __forceinline__ int idx() const {
@@ -262,7 +291,7 @@ template <int Q, int P, int L, int LD, bool FAST, typename T, class NB>
 __device__ __forceinline__ void load_cell(const KArgs& a, const NB& nb, const void* pop, T (&f)[Q]) {
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    f[k] = T(ldp<P>(pop, load_addr<Q, L, LD, k>(a, nb)));
+    f[k] = T(ldp<P>(a, pop, load_addr<Q, L, LD, k>(a, nb)));
   });
 }
 
@@ -281,7 +310,7 @@ __device__ __forceinline__ void store_cell_canonical(const KArgs& a, const Nb<FA
       const int cell = nb.template at<-cpos<Q, k>(0), -cpos<Q, k>(1), -cpos<Q, k>(2)>();
       ad = paddr<Q, L>(et_slot<Q, k, 0>(nb.template solid<Q, kb>()), cell, N);
     }
-    stp<P>(pop, ad, f[k]);
+    stp<P>(a, pop, ad, f[k]);
   });
 }
 
@@ -321,7 +350,12 @@ __device__ __forceinline__ uint32_t curved_links(const KArgs& a, const NB& nb, t
   using R = typename Store<P>::R;
   constexpr int H = Lat<Q>::H;
   if (!nb.curved) return 0u;
-  const double* q = a.qtab + (size_t)__ldg(a.qidx + nb.i) * Q;
+  const int row = __ldg(a.qidx + nb.i);
+  LBM_IF_DEBUG(if ((unsigned)row >= (unsigned)a.dbg_qrows) {
+    dbg_fault(a.dbg, DBG_CURVED, (unsigned)row);
+    return 0u;
+  })
+  const double* q = a.qtab + (size_t)row * Q;
   uint32_t done = 0u;
   static_for<0, H>([&](auto kc) {
     constexpr int km = decltype(kc)::value, kp = km + H + 1;
@@ -339,11 +373,11 @@ __device__ __forceinline__ uint32_t curved_links(const KArgs& a, const NB& nb, t
       } else {
         R fin;
         if constexpr (SK == K_ESOTWIST) {
-          fin = a.parity == 0 ? ldp<P>(a.a, load_addr<Q, L, LD_ET_EVEN, K>(a, nb))
-                              : ldp<P>(a.a, load_addr<Q, L, LD_ET_ODD, K>(a, nb));
+          fin = a.parity == 0 ? ldp<P>(a, a.a, load_addr<Q, L, LD_ET_EVEN, K>(a, nb))
+                              : ldp<P>(a, a.a, load_addr<Q, L, LD_ET_ODD, K>(a, nb));
         } else {
           constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : LD_LOCAL;
-          fin = ldp<P>(a.a, load_addr<Q, L, LD, K>(a, nb));
+          fin = ldp<P>(a, a.a, load_addr<Q, L, LD, K>(a, nb));
         }
         out = tq * fo + (R(1) - tq) * fin + W;
       }
@@ -367,24 +401,24 @@ __device__ __forceinline__ void step_store_nb(const KArgs& a, const NB& nb, cons
     constexpr int k = decltype(kc)::value;
     constexpr int kb = Lat<Q>::opp(k);
     if constexpr (k == Lat<Q>::REST) {
-      if constexpr (SK == K_TWOPOP) stp<P>(a.b, paddr<Q, L>(k, i, N), f[k]);
-      else stp<P>(a.a, paddr<Q, L>(k, i, N), f[k]);
+      if constexpr (SK == K_TWOPOP) stp<P>(a, a.b, paddr<Q, L>(k, i, N), f[k]);
+      else stp<P>(a, a.a, paddr<Q, L>(k, i, N), f[k]);
     } else {
       const bool bounce = nb.template solid<Q, k>();
       R v = f[k];
       if (bounce && !((done >> k) & 1u)) v = v + R(__ldg(a.wall + nb.template kind<Q, k>() * Q + k));
       if constexpr (SK == K_TWOPOP) {
-        if (!bounce) stp<P>(a.b, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
-        else stp<P>(a.b, paddr<Q, L>(kb, i, N), v);
+        if (!bounce) stp<P>(a, a.b, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
+        else stp<P>(a, a.b, paddr<Q, L>(kb, i, N), v);
       } else if constexpr (SK == K_AA_EVEN) {
-        stp<P>(a.a, paddr<Q, L>(kb, i, N), v);
+        stp<P>(a, a.a, paddr<Q, L>(kb, i, N), v);
       } else if constexpr (SK == K_AA_ODD) {
-        if (!bounce) stp<P>(a.a, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
-        else stp<P>(a.a, paddr<Q, L>(kb, i, N), v);
+        if (!bounce) stp<P>(a, a.a, paddr<Q, L>(k, nb.template idx<Q, k>(), N), v);
+        else stp<P>(a, a.a, paddr<Q, L>(kb, i, N), v);
       } else {  // esoteric twist
         const int cell = nb.template at<cneg<Q, k>(0), cneg<Q, k>(1), cneg<Q, k>(2)>();
         const int slot = a.parity == 0 ? kb : k;
-        stp<P>(a.a, paddr<Q, L>(slot, cell, N), v);
+        stp<P>(a, a.a, paddr<Q, L>(slot, cell, N), v);
       }
     }
   });

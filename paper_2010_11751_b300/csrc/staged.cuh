@@ -153,6 +153,13 @@ __device__ __forceinline__ void stage_issue_lane(const KArgs& a, unsigned char* 
     if (hi > lo) {
       lo &= ~(long long)(G::ALIGN - 1);
       hi = (hi + G::ALIGN - 1) & ~(long long)(G::ALIGN - 1);
+      LBM_IF_DEBUG(if (lo < 0 || hi > (long long)Q * N + (long long)(STAGE_PAD_BYTES / G::ES) ||
+                       hi - lo > G::SEG) {
+        dbg_fault(a.dbg, DBG_COPY_POP, (unsigned long long)(hi * G::ES));
+        s_off[lane] = 0;
+        mbar_arrive(full);
+        return;
+      })
       const uint32_t bytes = (uint32_t)((hi - lo) * G::ES);
       s_off[lane] = (int)(start - lo);
       mbar_arrive_expect_tx(full, bytes);
@@ -164,6 +171,11 @@ __device__ __forceinline__ void stage_issue_lane(const KArgs& a, unsigned char* 
     }
   } else if (lane == Q) {
     const uint32_t fbytes = (uint32_t)((cnt + 15) & ~15);
+    LBM_IF_DEBUG(if (base + fbytes > N + (long long)STAGE_PAD_BYTES || fbytes > (uint32_t)TILE) {
+      dbg_fault(a.dbg, DBG_COPY_FLAGS, (unsigned long long)(base + fbytes));
+      mbar_arrive(full);
+      return;
+    })
     mbar_arrive_expect_tx(full, fbytes);
     bulk_copy_g2s(smem_addr(buf + Q * G::SEG_BYTES), a.flags + base, fbytes, full);
   }
@@ -266,6 +278,11 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
         static_for<0, Q>([&](auto kc) {
           constexpr int k = decltype(kc)::value;
           const auto* run = reinterpret_cast<const typename Store<P>::S*>(buf + k * G::SEG_BYTES);
+          LBM_IF_DEBUG(if ((unsigned)(s_off[k] + c) >= (unsigned)G::SEG) {
+            dbg_fault(a.dbg, DBG_STAGE_READ, (unsigned)(s_off[k] + c));
+            g[k] = R(0);
+            return;
+          })
           g[k] = Store<P>::to_r(run[s_off[k] + c]);
         });
       };

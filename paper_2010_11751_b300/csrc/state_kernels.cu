@@ -252,6 +252,10 @@ __device__ __forceinline__ void swap_cell(const KArgs& a, int i, uint8_t fl) {
     constexpr int kb = Lat<Q>::opp(k);
     if (!nb.template solid<Q, k>()) {
       const size_t p0 = paddr<Q, L>(kb, i, a.N), p1 = paddr<Q, L>(k, nb.template idx<Q, k>(), a.N);
+      LBM_IF_DEBUG(if (p0 >= a.dbg_elems || p1 >= a.dbg_elems) {
+        dbg_fault(a.dbg, DBG_POP_STORE, p0 >= a.dbg_elems ? p0 : p1);
+        return;
+      })
       const S t0 = pop[p0], t1 = pop[p1];
       pop[p0] = t1;
       pop[p1] = t0;

@@ -9,6 +9,7 @@ library is missing, loading raises.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 
@@ -16,6 +17,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY = os.path.join(_HERE, "liblbm.so")
+# the bounds-checked build of the same sources (three collision models; see build.py)
+LIBRARY_DEBUG = os.path.join(_HERE, "liblbm_debug.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_STATE, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 D3Q19, D3Q27 = 19, 27
@@ -37,16 +40,38 @@ class LBMError(RuntimeError):
 
 
 _lib = None
+_loaded = {}
 
 
 def lib() -> ctypes.CDLL:
-    """Load liblbm.so (raises if it has not been built)."""
+    """The library every call of this module goes to: liblbm.so, or liblbm_debug.so inside a
+    ``debug_library()`` block (raises if it has not been built)."""
     global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIBRARY):
-        raise LBMError(ERR_STATE, f"{LIBRARY} is missing; build it with paper_2010_11751_b300.build.build()")
-    L = ctypes.CDLL(LIBRARY)
+    if _lib is None:
+        _lib = _load(LIBRARY)
+    return _lib
+
+
+@contextlib.contextmanager
+def debug_library():
+    """Route every call of this module to liblbm_debug.so, the bounds-checked build, for the
+    duration of the block.  Handles made inside belong to that library and must be destroyed
+    inside the block."""
+    global _lib
+    prev = lib()
+    _lib = _load(LIBRARY_DEBUG)
+    try:
+        yield _lib
+    finally:
+        _lib = prev
+
+
+def _load(path) -> ctypes.CDLL:
+    if path in _loaded:
+        return _loaded[path]
+    if not os.path.exists(path):
+        raise LBMError(ERR_STATE, f"{path} is missing; build it with paper_2010_11751_b300.build.build()")
+    L = ctypes.CDLL(path)
     vp, dp, u8p = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
     i, d = ctypes.c_int, ctypes.c_double
     sigs = {
@@ -86,9 +111,11 @@ def lib() -> ctypes.CDLL:
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    L.lbm_debug_check.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.lbm_debug_check.restype = ctypes.c_int
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = ctypes.c_char_p
-    _lib = L
+    _loaded[path] = L
     return L
 
 
@@ -192,6 +219,20 @@ def lbm_bytes_per_cell_update(h):
     v = ctypes.c_double()
     _check(lib().lbm_bytes_per_cell_update(h, ctypes.byref(v)))
     return v.value
+
+
+# kinds of the fault word of lbm_debug_check (bits 56..63)
+DEBUG_FAULTS = {1: "population load", 2: "population store", 3: "cell index", 4: "flag read",
+                5: "solid-neighbour mask read", 6: "staged population copy", 7: "staged flag copy",
+                8: "staged run read", 9: "link-fraction row", 10: "padding canary"}
+
+
+def lbm_debug_check(h):
+    """First bounds fault the handle's kernels recorded since the last check (0: none), and the
+    padding canaries; only liblbm_debug.so has the checks (liblbm.so raises ERR_UNSUPPORTED)."""
+    w = ctypes.c_ulonglong()
+    _check(lib().lbm_debug_check(h, ctypes.byref(w)))
+    return w.value
 
 
 def lbm_step_sums(h, n):
@@ -356,6 +397,10 @@ class Lattice:
 
     def reduce(self):
         return lbm_reduce(self.h)
+
+    def debug_check(self):
+        """lbm_debug_check: the first recorded bounds fault (0: none); liblbm_debug.so only."""
+        return lbm_debug_check(self.h)
 
     def set_link_fractions(self, q):
         """Walls at a fraction q of their links ([Q][N] FP64, or None for halfway walls)."""

@@ -31,6 +31,15 @@ def test_every_declared_symbol_is_exported(L):
     assert not missing, missing
 
 
+def test_debug_library_exports_every_symbol(L):
+    """liblbm_debug.so (the bounds-checked build) has the same C ABI."""
+    from paper_2010_11751_b300 import build
+    build.build(debug=True)
+    so = ctypes.CDLL(L.LIBRARY_DEBUG)
+    missing = [n for n in _declared("lbm.h") if not hasattr(so, n)]
+    assert not missing, missing
+
+
 def test_invalid_arguments_rejected(L):
     fl = np.zeros(27, np.uint8)
     bad = [
