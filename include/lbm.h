@@ -120,6 +120,21 @@ extern "C" {
  * staged kernel exits, it always waits for its own copies in flight with the
  * default bound, whatever this value is. */
 #define LBM_PARAM_WAIT_CYCLES 4
+/* Range of the FP64 BGK-W2 and TRT fast path (collision arithmetic on the
+ * FP32 and integer pipes, exact integer moments; cells outside the range take
+ * the plain FP64 operator).  1: narrow -- populations in their weights'
+ * binades; 2: wide -- also the binades next to them, for faster flows (a
+ * Taylor-Green vortex at u0 = 0.05 runs ~3x faster), at ~2 % extra cost for
+ * flows that stay near the weights; 0 (default): auto -- after every state
+ * write (lbm_init_equilibrium with rho or u, lbm_set_populations) the
+ * library counts the fluid cells with a population outside its weight's
+ * binade and picks wide when they exceed 1 %; those calls then synchronise
+ * the stream.  Either range matches the FP64 oracle within 1e-12; results
+ * are bit-identical across schemes and layouts for a given range, but a
+ * lattice resumed from lbm_set_populations may pick another range than the
+ * run it was saved from (set 1 or 2 explicitly for bit-exact resumption).
+ * No effect on other models and storage precisions. */
+#define LBM_PARAM_FX_RANGE 5
 
 typedef struct lbm_s* lbm_t;
 
@@ -163,8 +178,8 @@ LBM_API int lbm_set_wall_velocity(lbm_t h, int flag, double ux, double uy, doubl
 LBM_API int lbm_set_link_fractions(lbm_t h, const double* q);
 
 /* Set LBM_PARAM_*.  omega and omega_bulk in (0, 2), omega_high in (0, 2],
- * lambda > 0, wait_cycles an integer in [1, 2^40].  Takes effect at the next
- * step. */
+ * lambda > 0, wait_cycles an integer in [1, 2^40], fx range 0, 1 or 2.
+ * Takes effect at the next step. */
 LBM_API int lbm_set_param(lbm_t h, int key, double value);
 
 /* All device work of this handle goes to this cudaStream_t (NULL: legacy default).

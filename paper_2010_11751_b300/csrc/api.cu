@@ -210,12 +210,13 @@ KArgs make_args(const lbm_s* h) {
   a.wplus = a.wminus + w;
   a.omega_high = h->omega_high;
   a.trt_minus = 1.0 / (0.5 + h->lambda / (1.0 / w - 0.5));
+  a.fx_wide = h->fx_wide ? 1 : 0;
   if (h->Q == 19) {
     derived_rates<19>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
-    a.dk = derived_dfk<19>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+    a.dk = derived_dfk<19>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd, h->fx_wide);
   } else {
     derived_rates<27>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
-    a.dk = derived_dfk<27>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd);
+    a.dk = derived_dfk<27>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd, h->fx_wide);
   }
   return a;
 }
@@ -244,13 +245,39 @@ int reset_populations(lbm_s* h) {
   return upload_wall(h);
 }
 
+// range of the FP64 BGK-W2 / TRT fast path (fx64.cuh) for the state just
+// written: forced by LBM_PARAM_FX_RANGE, or, in auto mode, wide when more than
+// 1 % of the fluid cells have a population outside its weight's binade (each
+// would take the FP64 operator in the narrow range).  Auto mode synchronises
+// the stream to read the count.
+int decide_fx_range(lbm_s* h, bool rest = false) {
+  const bool fx = h->prec == F64 && (h->model == BGK_W2 || h->model == TRT);
+  if (!fx || h->fx_mode != 0) {
+    h->fx_wide = fx && h->fx_mode == 2;
+    return LBM_OK;
+  }
+  if (!h->populated || rest) {
+    h->fx_wide = false;  // the rest state: every population equals its weight
+    return LBM_OK;
+  }
+  int* count = h->d_err + 1;
+  LBM_CUDA(cudaMemsetAsync(count, 0, sizeof(int), h->stream));
+  const KArgs a = make_args(h);
+  LBM_CUDA(launch_fx_range_count(h->Q, h->prec, h->layout, load_kind(h), a, count, h->stream));
+  int n = 0;
+  LBM_CUDA(cudaMemcpyAsync(&n, count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  h->fx_wide = (long long)n * 100 > h->nfluid;
+  return LBM_OK;
+}
+
 int init_eq_device(lbm_s* h, const double* rho, const double* u) {
   int rc = reset_populations(h);
   if (rc) return rc;
   KArgs a = make_args(h);
   LBM_CUDA(launch_init(h->Q, h->prec, h->layout, store_kind(h), nw4_equilibrium(h->model), a, rho, u, h->stream));
   h->populated = true;
-  return LBM_OK;
+  return decide_fx_range(h, !rho && !u);
 }
 
 int valid_omega(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
@@ -327,6 +354,8 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
   if (!flags) return fail(LBM_ERR_INVALID_ARG, "flags is NULL");
   for (long long i = 0; i < N; ++i)
     if (flags[i] > 7) return fail(LBM_ERR_INVALID_ARG, "flag values must be 0..7");
+  long long nfluid = 0;
+  for (long long i = 0; i < N; ++i) nfluid += flags[i] == 0;
 
   lbm_s* h = new lbm_s();
   h->Q = lattice;
@@ -334,6 +363,7 @@ int lbm_create(lbm_t* out, int lattice, int nx, int ny, int nz, int scheme, int 
   h->ny = ny;
   h->nz = nz;
   h->N = (int)N;
+  h->nfluid = nfluid;
   h->scheme = scheme;
   h->model = collision;
   h->omega = omega;
@@ -514,6 +544,10 @@ int lbm_set_param(lbm_t h, int key, double v) {
         return fail(LBM_ERR_INVALID_ARG, "wait_cycles must be in [1, 2^40]");
       h->wait_cycles = (long long)v;
       return LBM_OK;
+    case LBM_PARAM_FX_RANGE:
+      if (!(v == 0.0 || v == 1.0 || v == 2.0)) return fail(LBM_ERR_INVALID_ARG, "fx range must be 0, 1 or 2");
+      h->fx_mode = (int)v;
+      return decide_fx_range(h);
     default:
       return fail(LBM_ERR_INVALID_ARG, "unknown parameter key");
   }
@@ -769,7 +803,7 @@ int lbm_set_populations(lbm_t h, const double* f) {
   KArgs a = make_args(h);
   LBM_CUDA(launch_set(h->Q, h->prec, h->layout, store_kind(h), a, src, h->stream));
   h->populated = true;
-  return LBM_OK;
+  return decide_fx_range(h);
 }
 
 int lbm_reduce(lbm_t h, double* mass, double* energy) {

@@ -136,6 +136,7 @@ int upload_members(lbm_batch_s* b) {
     d.nz = h->nz;
     d.N = h->N;
     handle_rates(h, &d.rd, &d.rf);
+    d.fx_wide = h->fx_wide ? 1 : 0;
     LBM_IF_DEBUG(d.dbg = reinterpret_cast<unsigned long long*>(h->d_err + 2);)
   }
   if (n > b->cap_members) {

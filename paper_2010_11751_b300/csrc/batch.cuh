@@ -19,7 +19,7 @@ struct __align__(16) Member {
   const uint32_t* nbmask;
   const double* wall;
   int nx, ny, nz, N;
-  int pad_parity;   // unused
+  int fx_wide;      // FP64 BGK-W2 / TRT: the member runs the wide range of fx64.cuh
   int block_begin;  // first grid block of the member (within its parity class map)
   int pad0, pad1;
   // the member's relaxation rates in both arithmetic types, derived and rounded
@@ -90,11 +90,22 @@ __global__ void __launch_bounds__(256, BATCH_MIN_BLOCKS<Q, M, P>) batch_aa_kerne
   }
   __syncthreads();
   const int base = (blockIdx.x - mm->block_begin) * blockDim.x * b.cpt + threadIdx.x;
+  // a member's cells all take its own range of the FP64 fast path (fx64.cuh),
+  // as when it is stepped alone
+  auto cells = [&](auto wide) {
 #pragma unroll 1
-  for (int j = 0; j < b.cpt; ++j) {
-    const int i = base + j * blockDim.x;
-    if (i < a.N) step_one<Q, M, P, SOA, SK>(a, i, [&] { return s_cp; });
+    for (int j = 0; j < b.cpt; ++j) {
+      const int i = base + j * blockDim.x;
+      if (i < a.N) step_one<Q, M, P, SOA, SK, decltype(wide)::value>(a, i, [&] { return s_cp; });
+    }
+  };
+  if constexpr (FX_KERNELS<M, P>) {
+    if (mm->fx_wide) {
+      cells(std::true_type{});
+      return;
+    }
   }
+  cells(std::false_type{});
 }
 
 // sk: K_AA_EVEN or K_AA_ODD

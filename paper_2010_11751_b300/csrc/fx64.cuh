@@ -30,11 +30,24 @@
 // non-equilibrium, high Mach number), or one whose w E_k leaves W_c's binade,
 // is updated by the plain FP64 operator instead (the caller reloads its
 // populations in the second case: every scheme's step reads and writes a
-// cell's slots from the same thread, so they are still in memory).  Both
-// paths compute the update of Section 2.6 to within a few FP64 rounding
-// errors; which one a cell takes depends only on its own populations, so every
-// scheme (they differ only in where they load and store) still produces
-// bit-identical results.
+// cell's slots from the same thread, so they are still in memory).
+//
+// Wide range (WIDE, a per-lattice mode chosen by the host for flows whose
+// populations stray further from the weights, such as a Taylor-Green vortex
+// at u0 = 0.05): populations in the binades next to their weights' are taken
+// too (f_k / t_k in [0.28, 2.25) for the D3Q19 classes 1/18 and 1/36, [0.42,
+// 3.37) on D3Q27), on a grid twice as fine (2^-59, 2^-61): the significand
+// is shifted by the population's own exponent.  On D3Q27, whose W_c sit low
+// in their binades, a w E_k that leaves W_c's binade for one next to it is
+// moved there (rounded to nearest, ties to even, above; exact below) instead
+// of sending the cell to the FP64 operator.  The wide code is larger, and
+// costs the narrow flows ~2 % when compiled in, so the two are separate
+// instantiations.
+//
+// Both paths, in either mode, compute the update of Section 2.6 to within a
+// few FP64 rounding errors; which one a cell takes depends only on its own
+// populations and the lattice's mode, so every scheme (they differ only in
+// where they load and store) still produces bit-identical results.
 #pragma once
 #include <cstring>
 
@@ -64,32 +77,71 @@ __host__ __device__ constexpr double fx_pow2(int e) {
 }
 
 // exponent of the integer grid of the moments: the unit in the last place of
-// the smallest weight (1/36 for D3Q19, 1/216 for D3Q27)
-__host__ __device__ constexpr int fx_grid(int Q) { return Q == 19 ? -58 : -60; }
+// the smallest weight (1/36 for D3Q19, 1/216 for D3Q27); half of it in the
+// wide mode, so that the binade below each weight's is on the grid too
+__host__ __device__ constexpr int fx_grid(int Q, bool wide) { return (Q == 19 ? -58 : -60) - (wide ? 1 : 0); }
 
-// the lattice weight of population K as an FP64 bit pattern, and the shift
-// that takes its units in the last place to the grid
-template <int Q, int K>
+// the lattice weight of population K as an FP64 bit pattern, the shift that
+// takes its units in the last place to the grid, and its value on the grid
+template <int Q, int K, bool WIDE>
 struct FxW {
   static constexpr double t = Lat<Q>::w(K);
   static constexpr int e = fx_exp2_floor(t);
   static constexpr long long mant = (long long)(t * fx_pow2(52 - e));  // in [2^52, 2^53)
   static constexpr long long bits = ((long long)(1023 + e) << 52) | (mant - (1LL << 52));
   static constexpr unsigned hi_tag = (unsigned)(1023 + e) << 20;  // sign 0 and the exponent field
-  static constexpr int sh = e - 52 - fx_grid(Q);
-  static_assert(sh >= 0 && sh < 8, "weight not representable on the grid");
+  static constexpr int sh = e - 52 - fx_grid(Q, WIDE);
+  static_assert(sh >= (WIDE ? 1 : 0) && sh < 8, "weight not representable on the grid");
+  static constexpr long long grid = mant << sh;
 };
 
 // host: the class constants W_c = w t_c (= wt[c], as bit patterns) and the
 // factors that take grid units to W_c's units in the last place
-inline void fx_class_constants(int Q, const double (&wt)[4], DFK& k) {
+inline void fx_class_constants(int Q, bool wide, const double (&wt)[4], DFK& k) {
   for (int c = 0; c < 4; ++c) {
     const double W = wt[c];
     static_assert(sizeof(double) == sizeof(long long), "64-bit double");
     std::memcpy(&k.wbits[c], &W, sizeof W);
     const int e = W > 0.0 ? fx_exp2_floor(W) : 0;
-    k.yscale[c] = (float)fx_pow2(fx_grid(Q) + 52 - e);
+    k.yscale[c] = (float)fx_pow2(fx_grid(Q, wide) + 52 - e);
   }
+}
+
+// wide mode: deviation f - t_K of population K on the grid, exact, when f is
+// positive and in t_K's binade or one next to it; otherwise `bad` is set (and
+// the value is meaningless)
+template <int Q, int K>
+__device__ __forceinline__ long long fx_dev_wide(double f, bool& bad) {
+  using W = FxW<Q, K, true>;
+  // high word relative to that of 2^(e - 1), the bottom of the binade below
+  // t_K's: in [0, 3 2^20) for the three binades (a negative f has the sign
+  // bit set and falls outside)
+  constexpr unsigned LO = (unsigned)(1022 + W::e) << 20;
+  const unsigned hi = (unsigned)__double2hiint(f) - LO;
+  bad |= hi >= (3u << 20);
+  // significand shifted to the grid: by sh - 1, sh or sh + 1
+  const unsigned mhi = (hi & 0xfffffu) | 0x100000u;
+  const unsigned long long m = ((unsigned long long)mhi << 32) | (unsigned)__double2loint(f);
+  return (long long)(m << ((W::sh - 1) + ((hi >> 20) & 3u))) - W::grid;
+}
+
+// bit pattern of W_c + (the integer added to W_c's bit pattern), when that sum
+// left W_c's binade by one (b: the sum as added, wexp: W_c's biased exponent):
+// rounded to nearest, ties to even, in the binade above; exact in the one
+// below; `ok` cleared further away
+__device__ __forceinline__ long long fx_rebinade(long long b, long long wexp, bool& ok) {
+  constexpr long long MASK = (1LL << 52) - 1;
+  const long long d = (b >> 52) - wexp;
+  const long long w = b & MASK;
+  if (d == 1) {
+    // b = (wexp + 1, V - 2^53): the significand V in W_c's units, halved
+    const long long h = (w >> 1) + (w & (w >> 1) & 1);
+    return (b & ~MASK) + h;
+  }
+  // d == -1: b = (wexp - 1, V) with V < 2^52 in W_c's units; the binade below
+  // holds 2 V - 2^52 (needs V >= 2^51)
+  ok = ok && d == -1 && w >= (1LL << 51);
+  return b + w - (1LL << 52);
 }
 
 // nearest integer of a double-float (W_c's last-place units); ok stays true
@@ -101,26 +153,34 @@ __device__ __forceinline__ long long fx_units(DF y, bool& ok) {
 
 // outcome of collide_fx
 enum FxStatus : int {
-  FX_SKIPPED = 0,  // a population outside its weight's binade: f untouched, use the FP64 operator
+  FX_SKIPPED = 0,  // a population out of range: f untouched, use the FP64 operator
   FX_DONE = 1,     // f holds the post-collision populations
-  FX_REDO = 2      // some w E_k left W_c's binade: f is clobbered, reload it and use the FP64 operator
+  FX_REDO = 2      // some w E_k out of range: f is clobbered, reload it and use the FP64 operator
 };
 
-template <int Q, bool TRT_>
+template <int Q, bool TRT_, bool WIDE>
 __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSums* cs) {
   constexpr int H = Lat<Q>::H;
-  unsigned acc = 0u;
-  static_for<0, Q>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    acc |= (unsigned)__double2hiint(f[k]) ^ FxW<Q, k>::hi_tag;
-  });
-  if (acc & 0xfff00000u) return FX_SKIPPED;
+  // on D3Q27 the wide mode also moves w E_k to the binades next to W_c's
+  constexpr bool REBINADE = WIDE && Q == 27;
+  bool bad = false;
+  if constexpr (!WIDE) {
+    unsigned acc = 0u;
+    static_for<0, Q>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      acc |= (unsigned)__double2hiint(f[k]) ^ FxW<Q, k, false>::hi_tag;
+    });
+    if (acc & 0xfff00000u) return FX_SKIPPED;
+  }
   // exact moments on the grid: r = rho - 1, j
   long long r, jx = 0, jy = 0, jz = 0;
   {
     auto dev = [&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      return (long long)((unsigned long long)(__double_as_longlong(f[k]) - FxW<Q, k>::bits) << FxW<Q, k>::sh);
+      if constexpr (WIDE) return fx_dev_wide<Q, k>(f[k], bad);
+      else
+        return (long long)((unsigned long long)(__double_as_longlong(f[k]) - FxW<Q, k, false>::bits)
+                           << FxW<Q, k, false>::sh);
     };
     r = dev(std::integral_constant<int, H>{});
     static_for<0, H>([&](auto kc) {
@@ -137,7 +197,10 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
       if constexpr (ez == -1) jz -= d;
     });
   }
-  constexpr float GRID = (float)fx_pow2(fx_grid(Q));
+  if constexpr (WIDE) {
+    if (bad) return FX_SKIPPED;
+  }
+  constexpr float GRID = (float)fx_pow2(fx_grid(Q, WIDE));
   // rho = 1 + r, v = 1.5 j / rho (real units); A = r - v.j (grid units)
   const DF dr = i64_to_df(r);
   const DF rho = fast_two_sum(1.0f, fmul(dr.hi, GRID));
@@ -153,8 +216,8 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
     A = df_sub(dr, vj);
     if (cs) {
       // FP64 sums of the state read: rho = 1 + r, kinetic energy |j|^2 / (2 rho) = v.j / 3
-      cs->rho = __dadd_rn(1.0, __dmul_rn(__ll2double_rn(r), fx_pow2(fx_grid(Q))));
-      cs->ke = __dmul_rn(__dadd_rn((double)vj.hi, (double)vj.lo), fx_pow2(fx_grid(Q)) / 3.0);
+      cs->rho = __dadd_rn(1.0, __dmul_rn(__ll2double_rn(r), fx_pow2(fx_grid(Q, WIDE))));
+      cs->ke = __dmul_rn(__dadd_rn((double)vj.hi, (double)vj.lo), fx_pow2(fx_grid(Q, WIDE)) / 3.0);
     }
   }
   // per weight class c (in W_c's last-place units): the bit pattern of
@@ -169,9 +232,17 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
   DF kq{0.0f, 0.0f}, kqm{0.0f, 0.0f}, kbd{0.0f, 0.0f};
   // w E_k = W_c + w t_c A + (e.v) q +- q, assembled on W_c's bit pattern; the
   // high words of every result are checked against W_c's sign and exponent
-  unsigned off = (unsigned)((base ^ k_.wbits[0]) >> 32);
+  unsigned off = 0u;
   const double omc = k_.omc64;
-  f[H] = fma(omc, f[H], __longlong_as_double(base));
+  {
+    long long b0 = base;
+    if constexpr (REBINADE) {
+      if ((b0 ^ k_.wbits[0]) >> 52) b0 = fx_rebinade(b0, k_.wbits[0] >> 52, ok);
+    } else {
+      off = (unsigned)((b0 ^ k_.wbits[0]) >> 32);
+    }
+    f[H] = fma(omc, f[H], __longlong_as_double(b0));
+  }
   static_for<0, H>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
@@ -206,13 +277,27 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
       // (1-w)/2 (f+ + f-) +- (1-w-)/2 (f+ - f-) = (1 - w) f+- -+ b d, with
       // b = (1-w)/2 - (1-w-)/2 and d = f+ - f- = g+ - g-: the difference of the
       // two bit patterns (both in t_k's binade), exact on the grid
-      constexpr int sh = FxW<Q, k>::sh;
-      const long long d = (long long)((unsigned long long)(__double_as_longlong(fp) - __double_as_longlong(fm)) << sh);
+      long long d;
+      if constexpr (WIDE) {
+        bool unused = false;  // both passed the range check of the moments
+        d = fx_dev_wide<Q, k + H + 1>(fp, unused) - fx_dev_wide<Q, k>(fm, unused);
+      } else {
+        constexpr int sh = FxW<Q, k, false>::sh;
+        d = (long long)((unsigned long long)(__double_as_longlong(fp) - __double_as_longlong(fm)) << sh);
+      }
       const long long bd = fx_units(df_mul(kbd, i64_to_df(d)), ok);
       bp -= bd;
       bm += bd;
     }
-    off |= (unsigned)((bp ^ k_.wbits[c]) >> 32) | (unsigned)((bm ^ k_.wbits[c]) >> 32);
+    if constexpr (REBINADE) {
+      if (((bp ^ k_.wbits[c]) >> 52) | ((bm ^ k_.wbits[c]) >> 52)) {
+        const long long wexp = k_.wbits[c] >> 52;
+        if ((bp ^ k_.wbits[c]) >> 52) bp = fx_rebinade(bp, wexp, ok);
+        if ((bm ^ k_.wbits[c]) >> 52) bm = fx_rebinade(bm, wexp, ok);
+      }
+    } else {
+      off |= (unsigned)((bp ^ k_.wbits[c]) >> 32) | (unsigned)((bm ^ k_.wbits[c]) >> 32);
+    }
     f[k + H + 1] = fma(omc, fp, __longlong_as_double(bp));
     f[k] = fma(omc, fm, __longlong_as_double(bm));
   });

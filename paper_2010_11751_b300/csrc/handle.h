@@ -36,6 +36,11 @@ struct lbm_s {
   double* d_sum_partials = nullptr;                 // their per-block partial sums
   size_t sum_partials_cap = 0;                      // doubles allocated there
   int* d_err = nullptr;        // [0] error word of the staged kernels, [1] scratch counter
+  // range of the FP64 BGK-W2 / TRT fast path (fx64.cuh): LBM_PARAM_FX_RANGE
+  // (0 auto, 1 narrow, 2 wide) and the range in use
+  int fx_mode = 0;
+  bool fx_wide = false;
+  long long nfluid = 0;        // fluid cells (flag 0)
   long long wait_cycles = 1LL << 32;  // bound of each staged-pipeline wait (SM clock cycles)
   // fluid cells with a non-zero flag byte (staged steps), sorted, and their records
   int* d_list = nullptr;

@@ -71,6 +71,9 @@ cudaError_t launch_get(int Q, int P, int L, int LD, const KArgs& a, double* out,
 cudaError_t launch_set(int Q, int P, int L, int LD, const KArgs& a, const double* in, cudaStream_t s);
 cudaError_t launch_init(int Q, int P, int L, int LD, bool nw4, const KArgs& a, const double* rho, const double* u,
                         cudaStream_t s);
+// add to *count the fluid cells of the FP64 state with a population outside its
+// weight's binade (the narrow range of fx64.cuh); FP64 storage only
+cudaError_t launch_fx_range_count(int Q, int P, int L, int LD, const KArgs& a, int* count, cudaStream_t s);
 int reduce_partials_count(int N);
 // out[0], out[1] = the sums of the n pairs of partials, in a fixed order
 cudaError_t launch_reduce_final(const double* partials, int n, double* out, cudaStream_t s);

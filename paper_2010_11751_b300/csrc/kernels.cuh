@@ -56,6 +56,9 @@ struct KArgs {
   // link fractions (-1: none), or null when the lattice has no such walls
   const int* qidx;
   const double* qtab;
+  // FP64 BGK-W2 / TRT: 1 when the lattice runs the wide range of fx64.cuh
+  // (a host decision per lattice; the launchers pick the kernel instantiation)
+  int fx_wide;
 #ifdef LBM_DEBUG
   unsigned long long* dbg;  // first failed bounds check (debug.cuh)
   size_t dbg_elems;         // populations in the array: Q N
@@ -83,7 +86,7 @@ __host__ __device__ inline void derived_rates(double omega, double trt_minus, do
 // the FP64 rates prepared for the FP32-pipe FP64 collisions (host)
 template <int Q>
 inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4], const double (&wm3)[4], double hs,
-                       double hd) {
+                       double hd, bool wide) {
   DFK k;
   k.omc = df_split(omc);
   k.hs = df_split(hs);
@@ -95,7 +98,7 @@ inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4]
     k.wm3[c] = df_split(wm3[c]);
     k.wm[c] = df_split(wm3[c] / 3.0);
   }
-  fx_class_constants(Q, wt, k);
+  fx_class_constants(Q, wide, wt, k);
   k.omc64 = omc;
   k.trt_a = hs + hd;
   k.trt_b = hs - hd;
@@ -472,12 +475,13 @@ __device__ __forceinline__ CP<typename Store<P>::R> rates(const KArgs& a) {
 // has one (fx64.cuh), the model's operator for the cells it declines;
 // reload(f) refills f with the cell's pre-collision populations (called only
 // when the first attempt had already overwritten them)
-template <int Q, int M, int P, class Reload>
+// (WIDE: the wide range of fx64.cuh)
+template <int Q, int M, int P, bool WIDE = false, class Reload>
 __device__ __forceinline__ void collide_cell(typename Store<P>::R (&f)[Q], const CP<typename Store<P>::R>& cp,
                                              CellSums* cs, Reload&& reload) {
   using R = typename Store<P>::R;
   if constexpr (HAS_FX<M, R, Store<P>::shifted>) {
-    const int st = collide_fx<Q, M == TRT>(f, cp.dk, cs);
+    const int st = collide_fx<Q, M == TRT, WIDE>(f, cp.dk, cs);
     if (st == FX_DONE) return;
     if (st == FX_REDO) reload(f);
   }
@@ -496,7 +500,7 @@ __device__ __forceinline__ bool curved_cell(const KArgs& a, int i, uint8_t fl) {
 // parameters without holding registers across the loads
 // cs (optional): receives the cell's share of the conserved sums of the state
 // it reads; left untouched for a solid cell
-template <int Q, int M, int P, int L, int SK, class RateFn>
+template <int Q, int M, int P, int L, int SK, bool WIDE = false, class RateFn>
 __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn, CellSums* cs = nullptr) {
   using R = typename Store<P>::R;
   R f[Q];
@@ -524,7 +528,7 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
   const CP<R> cp = rate_fn();
   // (a reload reads the cell's slots again: every scheme's step reads and
   // writes a cell's slots from this thread only, and it has written none yet)
-  collide_cell<Q, M, P>(f, cp, cs, [&](R (&g)[Q]) {
+  collide_cell<Q, M, P, WIDE>(f, cp, cs, [&](R (&g)[Q]) {
     if (fl == 0) step_load<Q, P, L, SK, true>(a, i, g);
     else step_load<Q, P, L, SK, false>(a, i, g, fl);
   });
@@ -548,11 +552,16 @@ inline constexpr int MIN_BLOCKS =
 // threads per block of the single-lattice step kernels
 inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }
 
-template <int Q, int M, int P, int L, int SK>
+// the FP64 BGK-W2 and TRT kernels come in two instantiations, the narrow and
+// the wide range of fx64.cuh (WIDE), which the launchers pick by a.fx_wide
+template <int M, int P>
+inline constexpr bool FX_KERNELS = HAS_FX<M, typename Store<P>::R, Store<P>::shifted>;
+
+template <int Q, int M, int P, int L, int SK, bool WIDE = false>
 __global__ void __launch_bounds__(256, MIN_BLOCKS<Q, M, P>) step_kernel(KArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
-  step_one<Q, M, P, L, SK>(a, i, [&] { return rates<P>(a); });
+  step_one<Q, M, P, L, SK, WIDE>(a, i, [&] { return rates<P>(a); });
 }
 
 using StepFn = cudaError_t (*)(const KArgs&, int threads, cudaStream_t);
@@ -574,7 +583,7 @@ __host__ __device__ constexpr int sum_cells_per_thread(int P) { return P == F64 
 template <int Q, int M, int P>
 inline constexpr int SUM_MIN_BLOCKS = P == F64 ? 2 : MIN_BLOCKS<Q, M, P>;
 
-template <int Q, int M, int P, int L, int SK>
+template <int Q, int M, int P, int L, int SK, bool WIDE = false>
 __global__ void __launch_bounds__(256, SUM_MIN_BLOCKS<Q, M, P>) step_sum_kernel(KArgs a, double* partials) {
   constexpr int CPT = sum_cells_per_thread(P);
   const int base = blockIdx.x * blockDim.x * CPT + threadIdx.x;
@@ -583,7 +592,7 @@ __global__ void __launch_bounds__(256, SUM_MIN_BLOCKS<Q, M, P>) step_sum_kernel(
   for (int j = 0; j < CPT; ++j) {
     const int i = base + j * (int)blockDim.x;
     CellSums cs{0.0, 0.0};
-    if (i < a.N) step_one<Q, M, P, L, SK>(a, i, [&] { return rates<P>(a); }, &cs);
+    if (i < a.N) step_one<Q, M, P, L, SK, WIDE>(a, i, [&] { return rates<P>(a); }, &cs);
     if (j == 0) {
       m = cs.rho;
       e = cs.ke;
@@ -618,6 +627,12 @@ template <int Q, int M, int P, int L, int SK>
 cudaError_t launch_step_sum(const KArgs& a, int threads, double* partials, cudaStream_t s) {
   const long long chunk = (long long)threads * sum_cells_per_thread(P);
   const int blocks = (int)((a.N + chunk - 1) / chunk);
+  if constexpr (FX_KERNELS<M, P>) {
+    if (a.fx_wide) {
+      step_sum_kernel<Q, M, P, L, SK, true><<<blocks, threads, 0, s>>>(a, partials);
+      return cudaGetLastError();
+    }
+  }
   step_sum_kernel<Q, M, P, L, SK><<<blocks, threads, 0, s>>>(a, partials);
   return cudaGetLastError();
 }
@@ -649,6 +664,12 @@ StepSumFn step_sum_fn_for_model(int Q, int P, int L, int SK) {
 template <int Q, int M, int P, int L, int SK>
 cudaError_t launch_step(const KArgs& a, int threads, cudaStream_t s) {
   const int blocks = (a.N + threads - 1) / threads;
+  if constexpr (FX_KERNELS<M, P>) {
+    if (a.fx_wide) {
+      step_kernel<Q, M, P, L, SK, true><<<blocks, threads, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   step_kernel<Q, M, P, L, SK><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -656,7 +677,7 @@ cudaError_t launch_step(const KArgs& a, int threads, cudaStream_t s) {
 // one step of the cells with walls at a fraction of their links (a list of n
 // cells), one thread each: load, collide, the interpolated reflections
 // (curved_links), store
-template <int Q, int M, int P, int L, int SK>
+template <int Q, int M, int P, int L, int SK, bool WIDE = false>
 __global__ void __launch_bounds__(128) curved_cells_kernel(KArgs a, const int* cells, int n) {
   using R = typename Store<P>::R;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -674,7 +695,7 @@ __global__ void __launch_bounds__(128) curved_cells_kernel(KArgs a, const int* c
     }
   };
   load(f);
-  collide_cell<Q, M, P>(f, rates<P>(a), nullptr, load);
+  collide_cell<Q, M, P, WIDE>(f, rates<P>(a), nullptr, load);
   const uint32_t done = curved_links<Q, P, L, SK>(a, nb, f);
   step_store_nb<Q, P, L, SK>(a, nb, f, done);
 }
@@ -682,6 +703,12 @@ __global__ void __launch_bounds__(128) curved_cells_kernel(KArgs a, const int* c
 template <int Q, int M, int P, int L, int SK>
 cudaError_t launch_curved(const KArgs& a, const int* cells, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if constexpr (FX_KERNELS<M, P>) {
+    if (a.fx_wide) {
+      curved_cells_kernel<Q, M, P, L, SK, true><<<(n + 127) / 128, 128, 0, s>>>(a, cells, n);
+      return cudaGetLastError();
+    }
+  }
   curved_cells_kernel<Q, M, P, L, SK><<<(n + 127) / 128, 128, 0, s>>>(a, cells, n);
   return cudaGetLastError();
 }

@@ -209,7 +209,8 @@ inline constexpr int STAGED_REGS =
 // partials[2 w], partials[2 w + 1] with w = blockIdx.x * CW + its index -- a
 // fixed assignment of cells to warps (the grid and its tile order are fixed),
 // so the sums are reproducible
-template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW, bool SUMS>
+// (WIDE: the wide range of the FP64 BGK-W2 / TRT collision, fx64.cuh)
+template <int Q, int M, int P, int SK, int TILE, int STAGES, int CW, bool SUMS, bool WIDE = false>
 __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
     staged_aa_kernel(KArgs a, int ntiles, int* err, long long wait_cycles, double* partials) {
   using G = StageLayout<Q, P, TILE, STAGES>;
@@ -289,11 +290,11 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
       fetch(f);
       if constexpr (SUMS) {
         CellSums cs{0.0, 0.0};
-        collide_cell<Q, M, P>(f, cp, &cs, fetch);  // a reload reads the stage again
+        collide_cell<Q, M, P, WIDE>(f, cp, &cs, fetch);  // a reload reads the stage again
         msum += cs.rho;
         esum += cs.ke;
       } else {
-        collide_cell<Q, M, P>(f, cp, nullptr, fetch);
+        collide_cell<Q, M, P, WIDE>(f, cp, nullptr, fetch);
       }
       step_store<Q, P, SOA, SK, true>(a, base + c, f);
     }
@@ -316,7 +317,7 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
 // the listed cells, one thread each, from their records.  SUMS: each 128-thread
 // block writes the FP64 mass and kinetic energy of its cells to
 // partials[2 b], partials[2 b + 1] (warp trees, then the four warps in order)
-template <int Q, int M, int P, int SK, bool SUMS>
+template <int Q, int M, int P, int SK, bool SUMS, bool WIDE = false>
 __global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed listed, double* partials) {
   using R = typename Store<P>::R;
   constexpr int LD = SK == K_AA_ODD ? LD_AA_ODD : LD_LOCAL;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(128) listed_cells_kernel(KArgs a, Listed liste
     R f[Q];
     load_cell<Q, P, SOA, LD, false>(a, nb, a.a, f);
     const CP<R> cp = rates<P>(a);
-    collide_cell<Q, M, P>(f, cp, SUMS ? &cs : nullptr,
+    collide_cell<Q, M, P, WIDE>(f, cp, SUMS ? &cs : nullptr,
                           [&](R (&g)[Q]) { load_cell<Q, P, SOA, LD, false>(a, nb, a.a, g); });
     const uint32_t done = curved_links<Q, P, SOA, SK>(a, nb, f);
     step_store_nb<Q, P, SOA, SK>(a, nb, f, done);
@@ -390,14 +391,16 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, 
   constexpr int threads = 32 * (1 + Sh::CW);
   constexpr bool can_sum = P == F64;
   if (nparts && !can_sum) return cudaErrorNotSupported;
-  auto kern = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, false>;
-  auto kern_sum = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, can_sum>;
+  constexpr bool fx = FX_KERNELS<M, P>;
+  auto kern_n = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, false>;
+  auto kern_sum_n = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, can_sum>;
+  auto kern_w = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, false, fx>;
+  auto kern_sum_w = staged_aa_kernel<Q, M, P, SK, Sh::TILE, Sh::STAGES, Sh::CW, can_sum, fx>;
   // blocks of the persistent grid: resident blocks per SM x SMs (set once)
   static const int grid = [&] {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) != cudaSuccess) return 0;
-    if (can_sum &&
-        cudaFuncSetAttribute(kern_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) != cudaSuccess)
-      return 0;
+    for (auto k : {kern_n, kern_sum_n, kern_w, kern_sum_w})
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) != cudaSuccess) return 0;
+    auto kern = kern_n;
     int occ = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, G::BYTES) != cudaSuccess) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -422,15 +425,20 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.side, ss.fork, 0);
     if (e != cudaSuccess) return e;
   }
+  const bool wide = fx && a.fx_wide;
   if (ntiles > 0) {
-    if (nparts) kern_sum<<<blocks, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles, partials);
-    else kern<<<blocks, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles, nullptr);
+    if (nparts) (wide ? kern_sum_w : kern_sum_n)<<<blocks, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles, partials);
+    else (wide ? kern_w : kern_n)<<<blocks, threads, G::BYTES, s>>>(a, ntiles, err, wait_cycles, nullptr);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || listed.n <= 0) return e;
   cudaStream_t ls = side ? ss.side : s;
-  if (nparts) listed_cells_kernel<Q, M, P, SK, can_sum><<<lblocks, 128, 0, ls>>>(a, listed, partials + 2 * blocks * Sh::CW);
-  else listed_cells_kernel<Q, M, P, SK, false><<<lblocks, 128, 0, ls>>>(a, listed, nullptr);
+  auto lk_n = listed_cells_kernel<Q, M, P, SK, false>;
+  auto lk_sum_n = listed_cells_kernel<Q, M, P, SK, can_sum>;
+  auto lk_w = listed_cells_kernel<Q, M, P, SK, false, fx>;
+  auto lk_sum_w = listed_cells_kernel<Q, M, P, SK, can_sum, fx>;
+  if (nparts) (wide ? lk_sum_w : lk_sum_n)<<<lblocks, 128, 0, ls>>>(a, listed, partials + 2 * blocks * Sh::CW);
+  else (wide ? lk_w : lk_n)<<<lblocks, 128, 0, ls>>>(a, listed, nullptr);
   e = cudaGetLastError();
   if (e == cudaSuccess && side) {
     e = cudaEventRecord(ss.join, ss.side);

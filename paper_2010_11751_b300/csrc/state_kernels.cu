@@ -375,6 +375,42 @@ cudaError_t launch_reduce(int Q, int P, int L, int LD, const KArgs& a, double* p
   return cudaGetLastError();
 }
 
+// the fluid cells of an FP64 state with a population outside its weight's
+// binade -- those the narrow range of the FP64 BGK-W2 / TRT fast path
+// (fx64.cuh) leaves to the FP64 operator -- added to *count
+template <int Q, int P, int L, int LD>
+__global__ void __launch_bounds__(256) fx_range_kernel(KArgs a, int* count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool out = false;
+  if (i < a.N) {
+    const uint8_t fl = a.flags[i];
+    if (!(fl & FLAG_KIND)) {
+      double f[Q];
+      load_canonical_f64<Q, P, L, LD>(a, i, fl, f);
+      unsigned acc = 0u;
+      static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        acc |= (unsigned)__double2hiint(f[k]) ^ FxW<Q, k, false>::hi_tag;
+      });
+      out = (acc & 0xfff00000u) != 0u;
+    }
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, out);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, __popc(b));
+}
+
+cudaError_t launch_fx_range_count(int Q, int P, int L, int LD, const KArgs& a, int* count, cudaStream_t s) {
+  if (P != F64) return cudaErrorInvalidValue;
+  const int blocks = (a.N + 255) / 256;
+  return dispatch_qpl(Q, P, L, [&](auto q, auto p, auto l) {
+    LBM_CONSTS(q, p, l);
+    return dispatch_ld(LD, [&](auto ld) {
+      fx_range_kernel<QQ, PP, LL, decltype(ld)::value><<<blocks, 256, 0, s>>>(a, count);
+      return cudaGetLastError();
+    });
+  });
+}
+
 cudaError_t launch_reduce_final(const double* partials, int n, double* out, cudaStream_t s) {
   reduce_final_kernel<<<1, 1024, 0, s>>>(partials, n, out);
   return cudaGetLastError();

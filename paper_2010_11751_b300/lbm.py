@@ -30,7 +30,8 @@ MODELS = {"BGK_W2": BGK_W2, "BGK_NW4": BGK_NW4, "TRT": TRT, "REG": REG, "RR": RR
 SOA, AOS = 0, 1
 F64, F32, F16 = 0, 1, 2
 PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}
-PARAM_OMEGA, PARAM_OMEGA_BULK, PARAM_OMEGA_HIGH, PARAM_TRT_LAMBDA, PARAM_WAIT_CYCLES = 0, 1, 2, 3, 4
+PARAM_OMEGA, PARAM_OMEGA_BULK, PARAM_OMEGA_HIGH, PARAM_TRT_LAMBDA, PARAM_WAIT_CYCLES, PARAM_FX_RANGE = 0, 1, 2, 3, 4, 5
+FX_AUTO, FX_NARROW, FX_WIDE = 0, 1, 2
 
 
 class LBMError(RuntimeError):
