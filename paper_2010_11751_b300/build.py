@@ -84,8 +84,11 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
     objdir = BUILD_DEBUG if debug else BUILD
     os.makedirs(objdir, exist_ok=True)
     srcs = _sources(debug)
-    # heaviest units first so the parallel build finishes sooner
-    srcs.sort(key=lambda s: ("model_k" not in s and "model_c" not in s and "model_rr" not in s, s))
+    # heaviest units first so the parallel build finishes sooner (the FP64 BGK-W2 and TRT
+    # kernels come in two ranges of their fast path)
+    heavy = ("model_bgk_w2.cu", "model_trt.cu", "model_k.cu", "model_cm.cu", "model_chm.cu", "model_rr.cu")
+    srcs.sort(key=lambda s: (os.path.basename(s) not in heavy, heavy.index(os.path.basename(s))
+                             if os.path.basename(s) in heavy else 0, s))
     jobs = jobs or max(1, os.cpu_count() or 1)
     flags = list(extra) + (["-DLBM_DEBUG"] if debug else [])
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
