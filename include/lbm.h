@@ -212,6 +212,17 @@ LBM_API int lbm_step(lbm_t h, int n);
  * errors as lbm_reduce. */
 LBM_API int lbm_step_sums(lbm_t h, int n, double* mass, double* energy);
 
+/* lbm_step_sums without the wait (no counterpart in the paper): enqueues the
+ * same work (n >= 1 steps; the sums of the state the call starts from) and
+ * returns at once.  out: 2 doubles {mass, energy}, device memory or
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister), written when
+ * the handle's stream reaches the copy; pageable host memory is rejected with
+ * LBM_ERR_INVALID_ARG.  A caller that keeps one call in flight while it reads
+ * the previous call's sums keeps the GPU busy.  Divergence shows as non-finite
+ * sums; a staged-wait timeout is reported by the next synchronous call
+ * (lbm_reduce, lbm_step_sums, lbm_get_populations to the host). */
+LBM_API int lbm_step_sums_async(lbm_t h, int n, double* out);
+
 /* rho[N] and u[3*N] (FP64) of the current pre-collision state; host or device.
  * Either may be NULL.  Synchronises the handle's stream for host outputs. */
 LBM_API int lbm_macroscopic(lbm_t h, double* rho, double* u);

@@ -692,17 +692,19 @@ int lbm_step(lbm_t h, int n) {
   return LBM_OK;
 }
 
-int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
-  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
-  if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
-  if (n == 0) return lbm_reduce(h, mass, energy);
+}  // extern "C"
+
+namespace {
+// enqueue lbm_step_sums' work on the handle's stream: the sums of the current
+// state land in the two doubles at *out2 (device memory of the handle)
+int enqueue_step_sums(lbm_s* h, int n, double** out2) {
   if (!h->populated) {
     int rc = init_eq_device(h, nullptr, nullptr);
     if (rc) return rc;
   }
   int rc = upload_wall(h);
   if (rc) return rc;
-  double* out2 = h->d_partials + 2 * h->partials;
+  *out2 = h->d_partials + 2 * h->partials;
   int parts = 0;
   rc = step_sum_parts(h, &parts);
   if (rc) return rc;
@@ -710,28 +712,37 @@ int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
     // no summing kernel for this configuration: the reduction kernel reads the
     // state first, then the steps run
     KArgs a = make_args(h);
-    LBM_CUDA(launch_reduce(h->Q, h->prec, h->layout, load_kind(h), a, h->d_partials, out2, h->stream));
-    rc = lbm_step(h, n);
-    if (rc) return rc;
-  } else {
-    const size_t need = 2 * (size_t)parts;
-    if (h->sum_partials_cap < need) {
-      if (h->d_sum_partials) {
-        LBM_CUDA(cudaStreamSynchronize(h->stream));
-        LBM_CUDA(cudaFree(h->d_sum_partials));
-        h->d_sum_partials = nullptr;
-        h->sum_partials_cap = 0;
-      }
-      LBM_CUDA(cudaMalloc(&h->d_sum_partials, sizeof(double) * need));
-      h->sum_partials_cap = need;
-    }
-    int nparts = 0;
-    rc = enqueue_step(h, h->d_sum_partials, &nparts);
-    if (rc) return rc;
-    LBM_CUDA(launch_reduce_final(h->d_sum_partials, nparts, out2, h->stream));
-    rc = lbm_step(h, n - 1);
-    if (rc) return rc;
+    LBM_CUDA(launch_reduce(h->Q, h->prec, h->layout, load_kind(h), a, h->d_partials, *out2, h->stream));
+    return lbm_step(h, n);
   }
+  const size_t need = 2 * (size_t)parts;
+  if (h->sum_partials_cap < need) {
+    if (h->d_sum_partials) {
+      LBM_CUDA(cudaStreamSynchronize(h->stream));
+      LBM_CUDA(cudaFree(h->d_sum_partials));
+      h->d_sum_partials = nullptr;
+      h->sum_partials_cap = 0;
+    }
+    LBM_CUDA(cudaMalloc(&h->d_sum_partials, sizeof(double) * need));
+    h->sum_partials_cap = need;
+  }
+  int nparts = 0;
+  rc = enqueue_step(h, h->d_sum_partials, &nparts);
+  if (rc) return rc;
+  LBM_CUDA(launch_reduce_final(h->d_sum_partials, nparts, *out2, h->stream));
+  return lbm_step(h, n - 1);
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return lbm_reduce(h, mass, energy);
+  double* out2 = nullptr;
+  int rc = enqueue_step_sums(h, n, &out2);
+  if (rc) return rc;
   double r[2];
   LBM_CUDA(cudaMemcpyAsync(r, out2, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -740,6 +751,23 @@ int lbm_step_sums(lbm_t h, int n, double* mass, double* energy) {
   rc = check_device_error(h);
   if (rc) return rc;
   if (!std::isfinite(r[0]) || !std::isfinite(r[1])) return fail(LBM_ERR_DIVERGED, "mass or energy is not finite");
+  return LBM_OK;
+}
+
+int lbm_step_sums_async(lbm_t h, int n, double* out) {
+  if (!h || !out) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(LBM_ERR_INVALID_ARG, "n must be >= 1");
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, out) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ERR_INVALID_ARG, "out must be device memory or page-locked host memory");
+  }
+  if (at.type == cudaMemoryTypeUnregistered)
+    return fail(LBM_ERR_INVALID_ARG, "out must be device memory or page-locked host memory");
+  double* out2 = nullptr;
+  int rc = enqueue_step_sums(h, n, &out2);
+  if (rc) return rc;
+  LBM_CUDA(cudaMemcpyAsync(out, out2, 2 * sizeof(double), cudaMemcpyDefault, h->stream));
   return LBM_OK;
 }
 

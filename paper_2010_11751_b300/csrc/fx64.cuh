@@ -151,6 +151,33 @@ __device__ __forceinline__ long long fx_units(DF y, bool& ok) {
   return df_round_i64(y);
 }
 
+// running sums of a summing kernel's cells kept off the FP64 pipe: the density
+// deviations rho - 1 and v.j (three times the kinetic energy) in grid units, as
+// renormalised double-float sums, and the number of cells (mass = n + r 2^grid,
+// kinetic energy = e 2^grid / 3)
+struct FxSums {
+  DF r, e;
+  int n;
+};
+
+// add a cell's FP64 sums (the FP64 operator's: rho, kinetic energy) to s
+template <int Q, bool WIDE>
+__device__ __forceinline__ void fx_sums_add_f64(FxSums& s, double rho, double ke) {
+  const double x = (rho - 1.0) * fx_pow2(-fx_grid(Q, WIDE));
+  const double y = ke * (3.0 * fx_pow2(-fx_grid(Q, WIDE)));
+  const float xh = __double2float_rn(x), yh = __double2float_rn(y);
+  s.r = df_renorm(df_add(s.r, DF{xh, __double2float_rn(x - (double)xh)}));
+  s.e = df_renorm(df_add(s.e, DF{yh, __double2float_rn(y - (double)yh)}));
+  s.n += 1;
+}
+
+// mass and kinetic energy of the sums
+template <int Q, bool WIDE>
+__device__ __forceinline__ void fx_sums_f64(const FxSums& s, double& mass, double& ke) {
+  mass = (double)s.n + ((double)s.r.hi + (double)s.r.lo) * fx_pow2(fx_grid(Q, WIDE));
+  ke = ((double)s.e.hi + (double)s.e.lo) * (fx_pow2(fx_grid(Q, WIDE)) / 3.0);
+}
+
 // outcome of collide_fx
 enum FxStatus : int {
   FX_SKIPPED = 0,  // a population out of range: f untouched, use the FP64 operator
@@ -158,8 +185,10 @@ enum FxStatus : int {
   FX_REDO = 2      // some w E_k out of range: f is clobbered, reload it and use the FP64 operator
 };
 
-template <int Q, bool TRT_, bool WIDE>
-__device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSums* cs) {
+// cs: the cell's FP64 sums (CellSums), or running sums to add the cell to
+// (FxSums; added unless the cell is skipped)
+template <int Q, bool TRT_, bool WIDE, class S>
+__device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, S* cs) {
   constexpr int H = Lat<Q>::H;
   // on D3Q27 the wide mode also moves w E_k to the binades next to W_c's
   constexpr bool REBINADE = WIDE && Q == 27;
@@ -215,9 +244,15 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, CellSum
     const DF vj = df_add(df_add(df_mul(vx, Jx), df_mul(vy, Jy)), df_mul(vz, Jz));
     A = df_sub(dr, vj);
     if (cs) {
-      // FP64 sums of the state read: rho = 1 + r, kinetic energy |j|^2 / (2 rho) = v.j / 3
-      cs->rho = __dadd_rn(1.0, __dmul_rn(__ll2double_rn(r), fx_pow2(fx_grid(Q, WIDE))));
-      cs->ke = __dmul_rn(__dadd_rn((double)vj.hi, (double)vj.lo), fx_pow2(fx_grid(Q, WIDE)) / 3.0);
+      // sums of the state read: rho = 1 + r, kinetic energy |j|^2 / (2 rho) = v.j / 3
+      if constexpr (std::is_same<S, FxSums>::value) {
+        cs->r = df_renorm(df_add(cs->r, dr));
+        cs->e = df_renorm(df_add(cs->e, vj));
+        cs->n += 1;
+      } else {
+        cs->rho = __dadd_rn(1.0, __dmul_rn(__ll2double_rn(r), fx_pow2(fx_grid(Q, WIDE))));
+        cs->ke = __dmul_rn(__dadd_rn((double)vj.hi, (double)vj.lo), fx_pow2(fx_grid(Q, WIDE)) / 3.0);
+      }
     }
   }
   // per weight class c (in W_c's last-place units): the bit pattern of

@@ -488,6 +488,25 @@ __device__ __forceinline__ void collide_cell(typename Store<P>::R (&f)[Q], const
   collide<Q, M, R, Store<P>::shifted, P == F32>(f, cp, cs);
 }
 
+// the collision of one cell in a summing FP64 BGK-W2 / TRT kernel: its sums of
+// the state read go to the running sums fs (fx64.cuh), off the FP64 pipe
+template <int Q, int M, int P, bool WIDE, class Reload>
+__device__ __forceinline__ void collide_cell_fxsums(double (&f)[Q], const CP<double>& cp, FxSums& fs,
+                                                    Reload&& reload) {
+  static_assert(HAS_FX<M, typename Store<P>::R, Store<P>::shifted>, "FP64 BGK-W2 / TRT only");
+  const int st = collide_fx<Q, M == TRT, WIDE>(f, cp.dk, &fs);
+  if (st == FX_DONE) return;
+  if (st == FX_REDO) {
+    // the fast path has added the cell's (exact) sums already
+    reload(f);
+    collide<Q, M, double, false, false>(f, cp, nullptr);
+    return;
+  }
+  CellSums cs{0.0, 0.0};
+  collide<Q, M, double, false, false>(f, cp, &cs);
+  fx_sums_add_f64<Q, WIDE>(fs, cs.rho, cs.ke);
+}
+
 // the cells with walls at a fraction of their links are updated by
 // curved_cells_kernel, after the step kernel (the cells of one step touch
 // disjoint memory, so which launch updates a cell does not matter)

@@ -256,7 +256,9 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
   // consumers: the bulk cells of each tile, from the staged runs
   const CP<R> cp = rates<P>(a);
   const int ct = threadIdx.x - 32;
-  double msum = 0.0, esum = 0.0;
+  // summing variants (FP64 BGK-W2 / TRT): the sums of the cells this thread
+  // updates, kept on the FP32 pipe (fx64.cuh)
+  FxSums fs{{0.0f, 0.0f}, {0.0f, 0.0f}, 0};
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int st = it % STAGES;
@@ -289,10 +291,7 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
       };
       fetch(f);
       if constexpr (SUMS) {
-        CellSums cs{0.0, 0.0};
-        collide_cell<Q, M, P, WIDE>(f, cp, &cs, fetch);  // a reload reads the stage again
-        msum += cs.rho;
-        esum += cs.ke;
+        collide_cell_fxsums<Q, M, P, WIDE>(f, cp, fs, fetch);  // a reload reads the stage again
       } else {
         collide_cell<Q, M, P, WIDE>(f, cp, nullptr, fetch);
       }
@@ -302,6 +301,8 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
     if (lane == 0) mbar_arrive(smem_addr(smem + 8 * (STAGES + st)));  // release stage st
   }
   if constexpr (SUMS) {
+    double msum, esum;
+    fx_sums_f64<Q, WIDE>(fs, msum, esum);
     for (int o = 16; o > 0; o >>= 1) {
       msum += __shfl_down_sync(0xffffffffu, msum, o);
       esum += __shfl_down_sync(0xffffffffu, esum, o);

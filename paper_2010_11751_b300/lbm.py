@@ -94,6 +94,7 @@ def _load(path) -> ctypes.CDLL:
         "lbm_bytes_per_cell_update": [vp, ctypes.POINTER(d)],
         "lbm_kernels_per_step": [vp, ctypes.POINTER(i)],
         "lbm_step_sums": [vp, i, ctypes.POINTER(d), ctypes.POINTER(d)],
+        "lbm_step_sums_async": [vp, i, dp],
         "lbm_destroy": [vp],
         "lbm_supported": [i, i, i, i, i],
         "lbm_conserved_sums_static": [i, i, dp, u8p, dp, vp],
@@ -220,6 +221,12 @@ def lbm_bytes_per_cell_update(h):
     v = ctypes.c_double()
     _check(lib().lbm_bytes_per_cell_update(h, ctypes.byref(v)))
     return v.value
+
+
+def lbm_step_sums_async(h, n, out):
+    """Enqueue lbm_step_sums' work; out (2 doubles, a device tensor or pinned host tensor)
+    receives {mass, energy} when the stream gets there."""
+    return _check(lib().lbm_step_sums_async(h, n, ptr(out)))
 
 
 # kinds of the fault word of lbm_debug_check (bits 56..63)
@@ -395,6 +402,10 @@ class Lattice:
     def step_sums(self, n=1):
         """(mass, energy) of the current state, then n steps: lbm_step_sums."""
         return lbm_step_sums(self.h, n)
+
+    def step_sums_async(self, out, n=1):
+        """lbm_step_sums_async: enqueue n steps; out receives the sums of the current state."""
+        lbm_step_sums_async(self.h, n, out)
 
     def reduce(self):
         return lbm_reduce(self.h)

@@ -262,6 +262,40 @@ def test_step_sums_fallback_and_zero_steps():
         assert g.reduce() == (m2, e2)
 
 
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+@pytest.mark.parametrize("model", ["BGK_W2", "K"])
+def test_step_sums_async_equals_step_sums(scheme, model):
+    """lbm_step_sums_async enqueues the work of lbm_step_sums: the same sums, bit for bit, into
+    pinned host or device memory, with one call kept in flight while the previous call's sums
+    are read; the same populations afterwards.  Pageable host memory is refused."""
+    torch = pytest.importorskip("torch")
+    Q, p = 19, prm()
+    flags, f0 = case(Q, DIMS, seed=171, model=model)
+    with gpu_lattice(Q, DIMS, flags, model, p, scheme) as g:
+        g.set_populations(f0)
+        sync = [g.step_sums(1) for _ in range(5)]
+        f_sync = g.get_populations().copy()
+    host = torch.empty((5, 2), dtype=torch.float64).pin_memory()
+    dev = torch.empty((5, 2), dtype=torch.float64, device="cuda")
+    for out in (host, dev):
+        with gpu_lattice(Q, DIMS, flags, model, p, scheme) as g:
+            g.set_populations(f0)
+            for i in range(5):
+                g.step_sums_async(out[i])
+            torch.cuda.synchronize()
+            assert [tuple(r) for r in out.cpu().tolist()] == sync
+            assert np.array_equal(g.get_populations(), f_sync)
+    with gpu_lattice(Q, DIMS, flags, model, p, scheme) as g:
+        g.set_populations(f0)
+        with pytest.raises(L.LBMError) as ei:
+            g.step_sums_async(np.zeros(2))
+        assert ei.value.code == L.ERR_INVALID_ARG
+        with pytest.raises(L.LBMError) as ei:
+            g.step_sums_async(host[0], n=0)
+        assert ei.value.code == L.ERR_INVALID_ARG
+        assert g.steps_done == 0
+
+
 @pytest.mark.parametrize("Q", [19, 27])
 @pytest.mark.parametrize("model", ["BGK_W2_EDU", "BGK_W2_LOOP"])
 @pytest.mark.parametrize("scheme", list(SCHEMES))
