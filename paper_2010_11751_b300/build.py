@@ -77,6 +77,38 @@ def _compile(src, extra, force=False, objdir=BUILD, reuse=True):
     return obj, r.stderr
 
 
+HEAVY = ("model_bgk_w2.cu", "model_trt.cu", "model_k.cu", "model_cm.cu", "model_chm.cu", "model_rr.cu")
+
+
+def _heaviest_first(item):
+    name = os.path.basename(item[0])
+    return (name not in HEAVY, HEAVY.index(name) if name in HEAVY else 0, item[2], name)
+
+
+def build_all(force: bool = False, jobs: int | None = None) -> tuple[str, str]:
+    """liblbm.so and liblbm_debug.so, their translation units compiled in one pool (heaviest
+    first), so that the two builds share the cores."""
+    todo = []
+    for debug in (False, True):
+        if force or not up_to_date(debug):
+            objdir = BUILD_DEBUG if debug else BUILD
+            os.makedirs(objdir, exist_ok=True)
+            todo += [(src, debug, objdir) for src in _sources(debug)]
+    if todo:
+        todo.sort(key=_heaviest_first)
+        jobs = jobs or max(1, os.cpu_count() or 1)
+        with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+            list(ex.map(lambda t: _compile(t[0], ["-DLBM_DEBUG"] if t[1] else [], force, t[2], reuse=True), todo))
+        for debug in sorted({t[1] for t in todo}):
+            objdir = BUILD_DEBUG if debug else BUILD
+            lib = LIB_DEBUG if debug else LIB
+            objs = [os.path.join(objdir, os.path.basename(src)[:-3] + ".o") for src in _sources(debug)]
+            tmp = lib + ".tmp"
+            subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
+            os.replace(tmp, lib)
+    return LIB, LIB_DEBUG
+
+
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra=(), debug=False) -> str:
     lib = LIB_DEBUG if debug else LIB
     if not force and up_to_date(debug):
@@ -86,9 +118,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
     srcs = _sources(debug)
     # heaviest units first so the parallel build finishes sooner (the FP64 BGK-W2 and TRT
     # kernels come in two ranges of their fast path)
-    heavy = ("model_bgk_w2.cu", "model_trt.cu", "model_k.cu", "model_cm.cu", "model_chm.cu", "model_rr.cu")
-    srcs.sort(key=lambda s: (os.path.basename(s) not in heavy, heavy.index(os.path.basename(s))
-                             if os.path.basename(s) in heavy else 0, s))
+    srcs.sort(key=lambda s: _heaviest_first((s, debug, "")))
     jobs = jobs or max(1, os.cpu_count() or 1)
     flags = list(extra) + (["-DLBM_DEBUG"] if debug else [])
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
