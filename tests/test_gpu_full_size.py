@@ -10,7 +10,10 @@
 * The same cavity with TRT in FP16 shifted storage: the staged AA step (persistent grid of
   two blocks per SM walking ~55 tiles each, plus the listed-cell kernel), 6 steps, within
   the FP16 short-run budget.
-* D3Q19 512^3 (the precision form's size) in FP32 and FP16, Taylor-Green and noisy cavity:
+* D3Q27 cavity 256^3 FP64 BGK-W2, AA (the staged step with three blocks per SM), 4 steps,
+  within 1e-12 (the bench line's D3Q27 form).
+* D3Q19 512^3 (the precision form's size) in FP64, FP32 and FP16, Taylor-Green (u0 = 0.05:
+  in FP64 the wide range of the BGK-W2 fast path) and noisy cavity:
   the oracle is too slow for whole 512^3 steps, so it steps windows of 24^3 cells cut from
   the GPU's state; after one step every cell at least one cell inside the window depends
   only on populations inside it (streaming moves one cell per step), so those cells are
@@ -35,10 +38,10 @@ THREADS = os.cpu_count() or 1
 LID = {I.LID: (0.02, 0.0, 0.0)}
 
 
-def _cavity(n, model, seed):
+def _cavity(n, model, seed, Q=19):
     flags = I.cavity_flags(n, n, n)
     omega = 1.0 / (3.0 * I.cavity_nu(0.02, n, 1000.0) + 0.5)
-    ref = O.Lattice(19, n, n, n, flags, model, O.params(omega), LID)
+    ref = O.Lattice(Q, n, n, n, flags, model, O.params(omega), LID)
     ref.init_equilibrium()
     ref.f *= I.noise(ref.f.shape, 0.05, seed=seed)
     ref.f[:, flags != 0] = 0.0
@@ -107,6 +110,18 @@ def test_cavity256_fp16_staged_aa_matches_oracle():
     assert _max_rel(got, ref.f, flags == 0) <= 3e-3
 
 
+def test_cavity256_d3q27_fp64_staged_aa_matches_oracle():
+    n = 256
+    flags, omega, ref = _cavity(n, "BGK_W2", seed=2563, Q=27)
+    with L.Lattice(27, n, n, n, "aa", "BGK_W2", omega, flags, wall_velocities=LID) as g:
+        assert L.lbm_kernels_per_step(g.h) == 2  # staged bulk kernel + listed-cell kernel
+        g.set_populations(ref.f)
+        g.step(4)
+        got = g.get_populations()
+    ref.step(4, nthreads=THREADS)
+    assert _max_rel(got, ref.f, flags == 0) <= 1e-12
+
+
 def _window(f_dev, flags, n, corner, w):
     x0, y0, z0 = corner
     fw = f_dev.view(19, n, n, n)[:, x0:x0 + w, y0:y0 + w, z0:z0 + w].cpu().numpy().reshape(19, -1)
@@ -114,7 +129,8 @@ def _window(f_dev, flags, n, corner, w):
     return np.ascontiguousarray(fw), fl
 
 
-@pytest.mark.parametrize("precision,workload,tol", [("f32", "taylor_green", 2e-6), ("f32", "cavity", 2e-6),
+@pytest.mark.parametrize("precision,workload,tol", [("f64", "taylor_green", 1e-12), ("f64", "cavity", 1e-12),
+                                                    ("f32", "taylor_green", 2e-6), ("f32", "cavity", 2e-6),
                                                     ("f16", "taylor_green", 1e-3), ("f16", "cavity", 1e-3)])
 def test_512_windows_one_step_against_oracle(precision, workload, tol):
     import torch
