@@ -303,15 +303,14 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, S* cs) 
     if constexpr (ey != 0) add_c(vy, ey);
     if constexpr (ez != 0) add_c(vz, ez);
     const DF qp = df_mul(kq, ev);                       // 3 w t (e.j), W_c units
-    const DF q = TRT_ ? df_mul(kqm, ev) : qp;           // antisymmetric part
     const long long pi = fx_units(df_mul(ev, qp), ok);  // (e.v) 3 w t (e.j)
-    const long long qi = fx_units(q, ok);
-    long long bp = base + pi + qi, bm = base + pi - qi;
     const double fp = f[k + H + 1], fm = f[k];
+    long long qi;  // antisymmetric part, +- in the pair
     if constexpr (TRT_) {
       // (1-w)/2 (f+ + f-) +- (1-w-)/2 (f+ - f-) = (1 - w) f+- -+ b d, with
       // b = (1-w)/2 - (1-w-)/2 and d = f+ - f- = g+ - g-: the difference of the
-      // two bit patterns (both in t_k's binade), exact on the grid
+      // two bit patterns (both in t_k's binade), exact on the grid; the
+      // antisymmetric part 3 w- t (e.j) - b d is rounded once
       long long d;
       if constexpr (WIDE) {
         bool unused = false;  // both passed the range check of the moments
@@ -320,10 +319,11 @@ __device__ __forceinline__ int collide_fx(double (&f)[Q], const DFK& k_, S* cs) 
         constexpr int sh = FxW<Q, k, false>::sh;
         d = (long long)((unsigned long long)(__double_as_longlong(fp) - __double_as_longlong(fm)) << sh);
       }
-      const long long bd = fx_units(df_mul(kbd, i64_to_df(d)), ok);
-      bp -= bd;
-      bm += bd;
+      qi = fx_units(df_sub(df_mul(kqm, ev), df_mul(kbd, i64_to_df(d))), ok);
+    } else {
+      qi = fx_units(qp, ok);
     }
+    long long bp = base + pi + qi, bm = base + pi - qi;
     if constexpr (REBINADE) {
       if (((bp ^ k_.wbits[c]) >> 52) | ((bm ^ k_.wbits[c]) >> 52)) {
         const long long wexp = k_.wbits[c] >> 52;
