@@ -37,21 +37,23 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 # FP64 pipe operations (DADD, DMUL, DFMA thread instructions) per fluid-cell update of the AA step
 # kernels, D3Q19/D3Q27 cavity 128^3, from one ncu capture per model (the even and odd kernels execute
-# the same counts).  The plain FP64 operators (RR, K, ...) are bound by the FP64 pipe, which issues
-# one of them per slot, so their roofline counts operations (flops are reported beside).  BGK-W2 and
-# TRT run their collision on the FP32 and integer pipes (exact integer moments, double-float
-# equilibrium) and keep one or two FP64 FMAs per population: they are bound by memory.
+# the same counts).  The plain FP64 operators (K, ...) are bound by the FP64 pipe, which issues
+# one of them per slot, so their roofline counts operations (flops are reported beside).  BGK-W2,
+# TRT and RR run their collision on the FP32 and integer pipes (exact integer moments,
+# double-float arithmetic; BGK-W2 and TRT keep one FP64 FMA per population, RR none): their
+# roofline is memory's (RR is bound by instruction issue short of it).
 FP64_OPS_PER_FLUID_CELL = {
     # (lattice, collision): (dadd, dmul, dfma) per fluid cell
     (19, "BGK_W2"): (0.24, 0.00, 19.00),
     (19, "TRT"): (0.24, 0.00, 19.00),
-    (19, "RR"): (74.24, 40.00, 96.00),
+    (19, "RR"): (0.24, 0.00, 0.00),
     (19, "K"): (81.24, 31.00, 111.00),
     (27, "BGK_W2"): (0.43, 0.00, 27.00),
+    (27, "RR"): (0.43, 0.00, 0.00),
     (27, "K"): (161.43, 67.00, 187.00),
 }
 # models whose FP64 collision runs off the FP64 pipe (memory-bound roofline)
-FP64_OFF_PIPE = {"BGK_W2", "TRT"}
+FP64_OFF_PIPE = {"BGK_W2", "TRT", "RR"}
 # B300 FP64 pipe: 2 DFMA (or DADD / DMUL) per SM per clock (ncu peak_sustained)
 FP64_OPS_PER_SM_CLK = 2
 # time budget of the reference arm (the FP64 CPU oracle timed on the host cores)

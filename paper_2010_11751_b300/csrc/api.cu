@@ -213,10 +213,10 @@ KArgs make_args(const lbm_s* h) {
   a.fx_wide = h->fx_wide ? 1 : 0;
   if (h->Q == 19) {
     derived_rates<19>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
-    a.dk = derived_dfk<19>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd, h->fx_wide);
+    a.dk = derived_dfk<19>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd, a.wplus, a.wminus, h->fx_wide);
   } else {
     derived_rates<27>(w, a.trt_minus, a.wt, a.wt3, a.wm3, a.hs, a.hd);
-    a.dk = derived_dfk<27>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd, h->fx_wide);
+    a.dk = derived_dfk<27>(a.omc, a.wt, a.wt3, a.wm3, a.hs, a.hd, a.wplus, a.wminus, h->fx_wide);
   }
   return a;
 }

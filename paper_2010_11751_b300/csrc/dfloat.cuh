@@ -192,6 +192,7 @@ struct DFK {
   double omc64;         // 1 - w
   double trt_a, trt_b;  // TRT: (1 - w)/2 + (1 - w-)/2 and (1 - w)/2 - (1 - w-)/2
   DF trt_bdf, pad2;     // trt_b as double-float
+  DF wplus, wminus;     // the bulk couplings w+ and w- (RR, fx_rr.cuh)
 };
 
 }  // namespace lbm

@@ -31,6 +31,7 @@
 
 #include "collision.cuh"
 #include "debug.cuh"
+#include "fx_rr.cuh"
 
 namespace lbm {
 
@@ -86,7 +87,7 @@ __host__ __device__ inline void derived_rates(double omega, double trt_minus, do
 // the FP64 rates prepared for the FP32-pipe FP64 collisions (host)
 template <int Q>
 inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4], const double (&wm3)[4], double hs,
-                       double hd, bool wide) {
+                       double hd, double wplus, double wminus, bool wide) {
   DFK k;
   k.omc = df_split(omc);
   k.hs = df_split(hs);
@@ -103,6 +104,8 @@ inline DFK derived_dfk(double omc, const double (&wt)[4], const double (&wt3)[4]
   k.trt_a = hs + hd;
   k.trt_b = hs - hd;
   k.trt_bdf = df_split(hs - hd);
+  k.wplus = df_split(wplus);
+  k.wminus = df_split(wminus);
   k.pad2 = {0.0f, 0.0f};
   return k;
 }
@@ -484,6 +487,10 @@ __device__ __forceinline__ void collide_cell(typename Store<P>::R (&f)[Q], const
     const int st = collide_fx<Q, M == TRT, WIDE>(f, cp.dk, cs);
     if (st == FX_DONE) return;
     if (st == FX_REDO) reload(f);
+  } else if constexpr (M == RR && P == F64) {
+    const int st = collide_rr_fx<Q>(f, cp.dk, cs);
+    if (st == FX_DONE) return;
+    if (st == FX_REDO) reload(f);
   }
   collide<Q, M, R, Store<P>::shifted, P == F32>(f, cp, cs);
 }
@@ -561,12 +568,13 @@ __device__ __forceinline__ void step_one(const KArgs& a, int i, RateFn&& rate_fn
 // measured fastest.  The moment models would spill under such caps: they keep
 // the default register budget.  FP64 kernels are capped at two blocks per SM
 // (<= 128 registers) so that a few warps per scheduler hide the FP64 pipe
-// latency; the D3Q19 BGK-W2 ones, whose collision runs mostly on the FP32 and
-// integer pipes (fx64.cuh) and is bound by latency, at three (<= 80 registers,
-// no spills: 10.4 -> 13.2 GLUPS for the 256^3 cavity; TRT would spill there).
+// latency; the D3Q19 BGK-W2 and RR ones, whose collisions run mostly on the
+// FP32 and integer pipes (fx64.cuh, fx_rr.cuh) and are bound by latency, at
+// three (<= 80 registers, no spills: BGK-W2 10.4 -> 13.2 GLUPS for the 256^3
+// cavity; TRT would spill there).
 template <int Q, int M, int P>
 inline constexpr int MIN_BLOCKS =
-    P == F64 ? ((Q == 19 && M == BGK_W2) ? 3 : 2)
+    P == F64 ? ((Q == 19 && (M == BGK_W2 || M == RR)) ? 3 : 2)
              : (!(M == BGK_W2 || M == TRT || M == REG) ? 1 : (Q == 19 ? (M == TRT ? 5 : 6) : 4));
 // threads per block of the single-lattice step kernels
 inline constexpr int step_threads(int P) { return P == F64 ? 256 : 128; }

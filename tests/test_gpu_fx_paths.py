@@ -179,3 +179,51 @@ def test_fast_taylor_green_matches_oracle(Q, model):
             g.step(30)
             cav[fx_range] = g.get_populations()
     assert np.array_equal(cav[0], cav[1])
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_rr_routes_match_oracle(Q):
+    """The recursive-regularized collision in FP64 takes the same integer / double-float route
+    (fx_rr.cuh) for cells whose populations lie in their weights' binades, and the FP64 operator
+    for the others (and for cells whose new populations would leave them): the five kinds of cell
+    above, mixed in every warp, against the oracle within 1e-12 after one and five steps, every
+    scheme bit-identical to the two-population one."""
+    flags, kind, f0, c, t = _mixed_state(Q, seed=2907 + Q)
+    in_reach, in_binade, _, _ = _classify(Q, flags, f0, c, t)
+    k = kind[flags == 0]
+    assert np.all(in_binade[k == 0]) and not np.any(in_binade[k == 3])
+    p = dict(omega=OMEGA, omega_bulk=1.2, omega_high=1.0, trt_lambda=0.25)
+    for steps in (1, 5):
+        lat = O.Lattice(Q, *DIMS, flags, "RR", O.params(OMEGA, 1.2, 1.0, 0.25), WALLS)
+        lat.f = f0.copy()
+        lat.step(steps)
+        base = _run(Q, DIMS, flags, "RR", p, f0, steps, 0)
+        fluid = flags == 0
+        ref, got = lat.f[:, fluid], base[:, fluid]
+        small = np.abs(ref) < 0.1 * t[:, None]
+        scale = np.where(small, t[:, None], np.abs(ref))
+        assert np.max(np.abs(got - ref) / scale) <= RTOL_F64, steps
+        for scheme in ("aa", "swap", "esotwist"):
+            got = _run(Q, DIMS, flags, "RR", p, f0, steps, 0, scheme=scheme)
+            assert np.array_equal(got, base), (scheme, steps)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_rr_cavity_near_rest_takes_the_fast_route(Q):
+    """A cavity near rest: every cell stays in its weights' binades, the RR update is the
+    integer / double-float one; 20 steps of a 20^3 cavity at Re 100 against the oracle."""
+    n = 20
+    flags = I.cavity_flags(n, n, n)
+    omega = 1.0 / (3.0 * I.cavity_nu(0.02, n, 100.0) + 0.5)
+    lid = {I.LID: (0.02, 0.0, 0.0)}
+    ref = O.Lattice(Q, n, n, n, flags, "RR", O.params(omega), lid)
+    ref.init_equilibrium()
+    ref.step(20)
+    from paper_2010_11751_b300 import lbm as L
+
+    with L.Lattice(Q, n, n, n, "aa", "RR", omega, flags, wall_velocities=lid) as g:
+        g.init_equilibrium()
+        g.step(20)
+        got = g.get_populations()
+    fluid = flags == 0
+    assert np.max(np.abs(got[:, fluid] - ref.f[:, fluid]) / np.abs(ref.f[:, fluid])) <= RTOL_F64
