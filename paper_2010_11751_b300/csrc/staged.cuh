@@ -291,7 +291,14 @@ __global__ void __maxnreg__((STAGED_REGS<Q, M, P, CW>))
       };
       fetch(f);
       if constexpr (SUMS) {
-        collide_cell_fxsums<Q, M, P, WIDE>(f, cp, fs, fetch);  // a reload reads the stage again
+        if constexpr (FX_KERNELS<M, P>) {
+          collide_cell_fxsums<Q, M, P, WIDE>(f, cp, fs, fetch);  // a reload reads the stage again
+        } else {
+          // RR: the cell's FP64 sums, added to the running sums
+          CellSums cs{0.0, 0.0};
+          collide_cell<Q, M, P, WIDE>(f, cp, &cs, fetch);
+          fx_sums_add_f64<Q, WIDE>(fs, cs.rho, cs.ke);
+        }
       } else {
         collide_cell<Q, M, P, WIDE>(f, cp, nullptr, fetch);
       }
@@ -448,17 +455,22 @@ cudaError_t launch_staged_step(const KArgs& a, int* err, long long wait_cycles, 
   return e;
 }
 
-// staged AA step of one model (SoA) for FP16 storage, and for FP64 BGK-W2 and
-// TRT; nullptr elsewhere.  FP16 populations are where it pays most: 2-byte loads
-// leave the one-thread-per-cell kernels short of bytes in flight.  The FP64
-// BGK-W2 and TRT collisions (fx64.cuh) keep ~80 registers per thread busy for
-// ~1300 instructions per cell, so the one-thread-per-cell kernels hold too few
-// loads in flight to cover HBM latency; staged, the copies are in flight
-// while the consumers compute.  FP32 keeps the one-thread-per-cell kernels
-// (they run near the HBM roof), as do the FP64 moment models (FP64-pipe bound).
+// staged AA step of one model (SoA) for FP16 storage, and for FP64 BGK-W2, TRT
+// and D3Q27 RR; nullptr elsewhere.  FP16 populations are where it pays most:
+// 2-byte loads leave the one-thread-per-cell kernels short of bytes in flight.
+// The FP64 BGK-W2, TRT and RR collisions (fx64.cuh, fx_rr.cuh) keep ~80
+// registers per thread busy for 1100 to 4300 instructions per cell, so the
+// one-thread-per-cell kernels hold too few loads in flight to cover HBM
+// latency; staged, the copies are in flight while the consumers compute.  D3Q19
+// RR is bound by instruction issue: staged (three 5-warp blocks per SM, as its
+// registers allow) it ran at 8.4 GLUPS against 10.1 for the one-thread-per-cell
+// kernel's 24 warps per SM, so it keeps that kernel.  FP32 keeps the
+// one-thread-per-cell kernels (they run near the HBM roof), as do the other FP64
+// moment models (FP64-pipe bound).
 template <int M>
 StagedFn staged_fn_for_model(int Q, int P, int SK) {
-  constexpr bool fx = M == BGK_W2 || M == TRT;
+  constexpr bool fx = M == BGK_W2 || M == TRT || M == RR;
+  constexpr bool fx19 = M == BGK_W2 || M == TRT;
   auto pick = [&](auto q, auto pp) -> StagedFn {
     constexpr int QQ = decltype(q)::value, PP = decltype(pp)::value;
     if (SK == K_AA_EVEN) return &launch_staged_step<QQ, M, PP, K_AA_EVEN>;
@@ -470,8 +482,12 @@ StagedFn staged_fn_for_model(int Q, int P, int SK) {
   if (P == F16) return Q == 19 ? pick(I19{}, std::integral_constant<int, F16>{})
                                : (Q == 27 ? pick(I27{}, std::integral_constant<int, F16>{}) : nullptr);
   if constexpr (fx) {
-    if (P == F64) return Q == 19 ? pick(I19{}, std::integral_constant<int, F64>{})
-                                 : (Q == 27 ? pick(I27{}, std::integral_constant<int, F64>{}) : nullptr);
+    if (P == F64) {
+      if (Q == 27) return pick(I27{}, std::integral_constant<int, F64>{});
+      if constexpr (fx19) {
+        if (Q == 19) return pick(I19{}, std::integral_constant<int, F64>{});
+      }
+    }
   }
   return nullptr;
 }
