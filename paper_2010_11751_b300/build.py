@@ -70,8 +70,7 @@ def _compile(src, extra, force=False, objdir=BUILD, reuse=True):
         t = os.path.getmtime(obj)
         if all(os.path.getmtime(p) <= t for p in [src, os.path.abspath(__file__)] + _headers()):
             return obj, ""
-    split = SPLIT.get(os.path.basename(src))
-    cmd = [_nvcc()] + FLAGS + ARCH + extra + ([f"-split-compile={split}"] if split else []) + ["-c", src, "-o", obj]
+    cmd = [_nvcc()] + FLAGS + ARCH + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -79,10 +78,7 @@ def _compile(src, extra, force=False, objdir=BUILD, reuse=True):
 
 
 HEAVY = ("model_rr.cu", "model_bgk_w2.cu", "model_trt.cu", "model_k.cu", "model_cm.cu", "model_chm.cu")
-# the units whose FP64 kernels carry both the integer / double-float collision and the FP64
-# operator in every step, staged, listed-cell, summing, curved-wall and batch kernel: their device
-# code is compiled in several threads (nvcc -split-compile), so that they do not hold up the build
-SPLIT = {"model_rr.cu": 4, "model_bgk_w2.cu": 2, "model_trt.cu": 2}
+
 
 
 def _heaviest_first(item):
