@@ -256,9 +256,9 @@ LBM_API int lbm_bytes_per_cell_update(lbm_t h, double* bytes);
 /* Number of kernel launches one time step of the handle makes (*n >= 1):
  * 1 for the one-thread-per-cell kernels; 2 for swap (collision, then the
  * streaming pass) and for the staged AA steps of SoA storage in FP16 (every
- * model) and in FP64 (BGK-W2 and TRT): the shared-memory-staged kernel over
- * the bulk cells, then the kernel over the cells next to a wall or on a domain
- * face, if there are any.  May build the latter's cell list (device memory it
+ * model) and in FP64 (BGK-W2 and TRT, and RR on D3Q27): the
+ * shared-memory-staged kernel over the bulk cells, then the kernel over the
+ * cells next to a wall or on a domain face, if there are any.  May build the latter's cell list (device memory it
  * owns; see lbm_device_bytes). */
 LBM_API int lbm_kernels_per_step(lbm_t h, int* n);
 
