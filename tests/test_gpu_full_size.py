@@ -11,7 +11,7 @@
   two blocks per SM walking ~55 tiles each, plus the listed-cell kernel), 6 steps, within
   the FP16 short-run budget.
 * D3Q27 cavity 256^3 FP64 BGK-W2, AA (the staged step with three blocks per SM), 4 steps,
-  within 1e-12 (the bench line's D3Q27 form).
+  within 1e-12 (the bench line's D3Q27 form); D3Q19 256^3 RR (the matrix's size), 4 steps.
 * D3Q19 512^3 (the precision form's size) in FP64, FP32 and FP16, Taylor-Green (u0 = 0.05:
   in FP64 the wide range of the BGK-W2 fast path) and noisy cavity:
   the oracle is too slow for whole 512^3 steps, so it steps windows of 24^3 cells cut from
@@ -115,6 +115,20 @@ def test_cavity256_d3q27_fp64_staged_aa_matches_oracle():
     flags, omega, ref = _cavity(n, "BGK_W2", seed=2563, Q=27)
     with L.Lattice(27, n, n, n, "aa", "BGK_W2", omega, flags, wall_velocities=LID) as g:
         assert L.lbm_kernels_per_step(g.h) == 2  # staged bulk kernel + listed-cell kernel
+        g.set_populations(ref.f)
+        g.step(4)
+        got = g.get_populations()
+    ref.step(4, nthreads=THREADS)
+    assert _max_rel(got, ref.f, flags == 0) <= 1e-12
+
+
+def test_cavity256_rr_fp64_matches_oracle():
+    """The recursive-regularized collision at the matrix's size: D3Q19 256^3 noisy cavity, AA
+    (its one-thread-per-cell kernels, the integer / double-float route for most cells), 4 steps,
+    within 1e-12."""
+    n = 256
+    flags, omega, ref = _cavity(n, "RR", seed=2564)
+    with L.Lattice(19, n, n, n, "aa", "RR", omega, flags, wall_velocities=LID) as g:
         g.set_populations(ref.f)
         g.step(4)
         got = g.get_populations()
